@@ -1,0 +1,153 @@
+"""Pins for the oracle's FP64 CG / GMRES(30) and the stepped solvers (Alg. 3,
+Sec. III-D): textbook invariants, dense LU solves and the CG error bound."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+
+def _solve_dense(A):
+    return np.linalg.solve(A.dense(), synth.rhs_ones(A))
+
+
+def test_cg_invariants_on_spd():
+    A = synth.laplace2d(14, 13, shift=0.05, aniso=(1.0, 0.3))
+    b = synth.rhs_ones(A)
+    T = 12
+    out = oracle.cg(A.row_ptr, A.col, A.val, b, tol=1e-300, max_iter=T - 1, trace_n=T)
+    D = A.dense()
+    R, Pm, X = out["r"], out["p"], out["xs"]
+    xs = np.linalg.solve(D, b)
+    for i in range(T - 1):
+        for j in range(i):
+            # residuals mutually orthogonal, directions A-conjugate
+            assert abs(R[i] @ R[j]) <= 1e-9 * np.linalg.norm(R[i]) * np.linalg.norm(R[j])
+            assert abs(Pm[i] @ D @ Pm[j]) <= 1e-9 * np.sqrt((Pm[i] @ D @ Pm[i]) * (Pm[j] @ D @ Pm[j]))
+    errA = [np.sqrt((xs - X[i]) @ D @ (xs - X[i])) for i in range(T)]
+    assert all(errA[i + 1] <= errA[i] * (1 + 1e-12) for i in range(T - 1))
+    # textbook bound ||e_j||_A <= 2 ((sqrt(k)-1)/(sqrt(k)+1))^j ||e_0||_A
+    ev = np.linalg.eigvalsh(D)
+    rho = (np.sqrt(ev[-1] / ev[0]) - 1) / (np.sqrt(ev[-1] / ev[0]) + 1)
+    assert all(errA[j] <= 2 * rho ** j * errA[0] * (1 + 1e-10) for j in range(T))
+
+
+def test_cg_solution_and_iteration_count():
+    A = synth.poisson2d(32)
+    b = synth.rhs_ones(A)
+    out = oracle.cg(A.row_ptr, A.col, A.val, b, tol=1e-10, max_iter=5000)
+    info = out["info"]
+    assert info["status"] == oracle.OK and info["rel_res_true"] < 1e-9
+    assert np.max(np.abs(out["x"] - 1.0)) < 1e-7
+    # kappa(5-point Poisson 32x32) = cot^2(pi/(2*33)) ~ 441; the A-norm bound
+    # caps CG at sqrt(kappa)/2 * ln(2/tol) ~ 250 iterations (b = A*1 is smooth,
+    # so it needs far fewer)
+    kappa = 1 / np.tan(np.pi / 66) ** 2
+    assert 10 < info["iters"] <= int(np.sqrt(kappa) / 2 * np.log(2 / 1e-10)) + 10
+
+
+def test_gmres_invariants_and_dense_solve():
+    rng = np.random.default_rng(5)
+    A = synth.convdiff2d(7, peclet=50.0)
+    D = A.dense()
+    b = rng.uniform(-1, 1, A.n_rows)
+    m = 10
+    out = oracle.gmres(A.row_ptr, A.col, A.val, b, tol=1e-12, restart=m, max_iter=2000,
+                       want_first_cycle=True)
+    V, H = out["V"], out["H"]
+    assert np.linalg.norm(V @ V.T - np.eye(m + 1)) < 1e-12                   # orthonormal basis
+    assert np.linalg.norm(D @ V[:m].T - V.T @ H) < 1e-12 * np.linalg.norm(D)  # Arnoldi relation
+    assert out["info"]["status"] == oracle.OK
+    assert np.allclose(out["x"], np.linalg.solve(D, b), rtol=0, atol=1e-9)
+
+
+def test_gmres_full_restart_finite_termination():
+    """With restart >= n GMRES reaches the solution in at most n steps."""
+    rng = np.random.default_rng(6)
+    n = 12
+    D = rng.normal(size=(n, n)) + n * np.eye(n)
+    rows, cols = np.nonzero(D)
+    rp = np.zeros(n + 1, np.int32)
+    np.cumsum(np.bincount(rows, minlength=n), out=rp[1:])
+    b = rng.normal(size=n)
+    out = oracle.gmres(rp, cols.astype(np.int32), D[rows, cols], b, tol=1e-13, restart=n, max_iter=n)
+    assert out["info"]["iters"] <= n
+    assert np.allclose(out["x"], np.linalg.solve(D, b), atol=1e-11)
+
+
+def test_gmres_residual_nonincreasing_within_cycles():
+    A = synth.convdiff2d(16, peclet=10.0)
+    b = synth.rhs_ones(A)
+    lv = oracle.levels(A.val)
+    pol = oracle.Policy(l=10 ** 9, t=30, m=30, rsd_limit=0.03, ndec_limit=8, reldec_limit=0.08,
+                        max_iter=3000, restart=30, k_start=3, k_max=3)
+    out = oracle.stepped_gmres(A.row_ptr, A.col, lv, b, tol=1e-10, policy=pol, hist_cap=3000)
+    h = out["hist"][: out["info"]["iters"]]
+    for c in range(0, h.size, 30):
+        seg = h[c:c + 30]
+        assert np.all(np.diff(seg) <= 1e-15)
+
+
+def test_stepped_cg_exact_head_never_steps():
+    """5-point Poisson with values 4 and -1 is exact in the head (A_1 = A), so
+    the stepped CG finishes at level 1 with the same answer as FP64 CG."""
+    A = synth.poisson2d(32)
+    b = synth.rhs_ones(A)
+    lv = oracle.levels(A.val)
+    assert np.array_equal(lv[0], A.val)
+    out = oracle.stepped_cg(A.row_ptr, A.col, lv, b, tol=1e-10, policy=oracle.SCALED_CG)
+    i = out["info"]
+    assert i["status"] == oracle.OK and i["k_final"] == 1 and i["switch_iter"][1] == -1
+    ref = oracle.cg(A.row_ptr, A.col, A.val, b, tol=1e-10)
+    assert i["iters"] == ref["info"]["iters"]
+    assert np.array_equal(out["x"], ref["x"])
+
+
+def test_stepped_cg_steps_to_level3_on_non_dyadic_values():
+    A = synth.poisson2d(32, scale=1.0 / 3.0)
+    b = synth.rhs_ones(A)
+    lv = oracle.levels(A.val)
+    assert not np.array_equal(lv[0], A.val)
+    out = oracle.stepped_cg(A.row_ptr, A.col, lv, b, tol=1e-10, policy=oracle.SCALED_CG, hist_cap=5000)
+    i = out["info"]
+    assert i["status"] == oracle.OK and i["k_final"] == 3
+    assert 0 < i["switch_iter"][1] < i["switch_iter"][2]
+    assert i["rel_res_true"] < 1e-10
+    # the true FP64 residual agrees (A_3 differs from A by < 2^-50 relative)
+    r = b - oracle.spmv(A.row_ptr, A.col, A.val, out["x"])
+    assert np.linalg.norm(r) / np.linalg.norm(b) < 2e-10
+    assert np.max(np.abs(out["x"] - 1.0)) < 1e-6
+
+
+def test_stepped_cg_level1_floor():
+    """Without stepping, CG on A_1 converges to A_1^-1 b: its true residual
+    stalls near ||(A - A_1) x|| / ||b||, far above 1e-10 (Sec. III-D's reason
+    to raise the precision)."""
+    A = synth.laplace3d(10, shift=1e-3)
+    b = synth.rhs_ones(A)
+    lv = oracle.levels(A.val)
+    out = oracle.cg(A.row_ptr, A.col, lv[0], b, tol=1e-12, max_iter=5000)
+    r = b - oracle.spmv(A.row_ptr, A.col, A.val, out["x"])
+    floor = np.linalg.norm(oracle.spmv(A.row_ptr, A.col, A.val - lv[0], out["x"])) / np.linalg.norm(b)
+    assert np.linalg.norm(r) / np.linalg.norm(b) == pytest.approx(floor, rel=1e-2)
+    assert floor > 1e-8
+
+
+def test_stepped_gmres_reaches_tol_at_level3():
+    A = synth.convdiff2d(24, peclet=10.0).scaled(1.0 / 3.0)
+    b = synth.rhs_ones(A)
+    lv = oracle.levels(A.val)
+    out = oracle.stepped_gmres(A.row_ptr, A.col, lv, b, tol=1e-10, policy=oracle.SCALED_GMRES)
+    i = out["info"]
+    assert i["status"] == oracle.OK and i["k_final"] == 3 and i["rel_res_true"] < 1e-10
+    ref = oracle.gmres(A.row_ptr, A.col, A.val, b, tol=1e-10)
+    assert np.allclose(out["x"], ref["x"], atol=1e-7)
+
+
+def test_zero_rhs():
+    A = synth.poisson2d(4)
+    b = np.zeros(A.n_rows)
+    lv = oracle.levels(A.val)
+    for f in (oracle.stepped_cg, oracle.stepped_gmres):
+        out = f(A.row_ptr, A.col, lv, b, x0=np.ones(A.n_rows), tol=1e-10, policy=oracle.SCALED_CG)
+        assert out["info"]["status"] == oracle.OK and np.all(out["x"] == 0)
