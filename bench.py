@@ -1,0 +1,382 @@
+#!/usr/bin/env python3
+"""Benchmark: GSE-SpMV GB/s and % of the HBM roofline per precision level k,
+and stepped-CG time-to-1e-10 against FP64 CSR CG on the same GPU.
+
+Workload (one "step"): GSE-SpMV at k = 1, 2, 3 on the 3D 7-point Laplacian
+128^3 (n = 2,097,152, nnz = 14,581,760) and on the random power-law matrix
+(n = 1,000,000, mean row length 16, max 2048, values +-10^U(-3,3)); x ~ U[-1,1],
+seeded.  L2 is flushed (a 256 MiB write) before every timed SpMV; each SpMV is
+timed with CUDA events on the launching stream.  After the timed steps, the
+FP64/FP32 CSR baselines of the same matrices and the solver comparison (config
+"3D 7-point Laplacian 192^3 + 1e-3 shift, CG to 1e-10") are measured once and
+reported beside the headline.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun (N > 1) every rank runs the same workload on its own GPU
+(replicas: the single-matrix SpMV does not shard) and rank 0 prints one line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "GSE-SpMV GB/s & % HBM roofline per k; stepped-CG time-to-1e-10 vs FP64 CSR CG"
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# FP64 FMA rate of this GB300 pool, measured by a DFMA throughput kernel
+# (8 independent FMA chains per thread, 2048 threads per SM): 0.59e12 FMA/s.
+DFMA_PEAK_PER_S = 0.59e12
+
+
+def algorithmic_bytes(nnz, n_rows, n_cols, k, seg=(16, 16, 20), G=32):
+    """col 4 B + live segments + group exponent per nonzero, row_ptr, x once, y once."""
+    return nnz * (4 + sum(seg[:k]) / 8.0 + 2.0 / G) + 4 * (n_rows + 1) + 8 * n_cols + 8 * n_rows
+
+
+def csr_bytes(nnz, n_rows, n_cols, vbytes):
+    return nnz * (4 + vbytes) + 4 * (n_rows + 1) + 8 * n_cols + 8 * n_rows
+
+
+def src_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2411_04686_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc:
+            time.sleep(0.3)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def build_workload():
+    A = synth.laplace3d(128)
+    B = synth.powerlaw_random(1_000_000, 16.0, 2048, seed=0)
+    return [("laplace3d_128", A), ("powerlaw_1m", B)]
+
+
+def run_reference(args):
+    """The oracle (plain single-thread C) on the host cores, same metric/unit."""
+    import oracle
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    mats = build_workload()
+    A = mats[0][1]
+    x = synth.uniform_x(A.n_cols, seed=0)
+    enc = oracle.encode(A.val)
+    oracle.build()
+    per_step_bytes = sum(algorithmic_bytes(A.nnz, A.n_rows, A.n_cols, k) for k in (1, 2, 3))
+    for _ in range(args.warmup):
+        oracle.gse_spmv(A.row_ptr, A.col, enc, 1, x)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for k in (1, 2, 3):
+            oracle.gse_spmv(A.row_ptr, A.col, enc, k, x)
+    dt = time.perf_counter() - t0
+    v = per_step_bytes * args.steps / dt / 1e9
+    sample = "GSE-SpMV k=1,2,3 on laplace3d_128 only (the power-law half of the step is skipped)"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": "GB/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": "gse_spmv_sweep_laplace3d128_powerlaw1m", "sample": sample},
+        "cpu_baseline": {"kind": "oracle", "value": round(v, 3), "unit": "GB/s", "cores": 1, "sample": sample},
+        "e2e": {"value": round(v, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def cpu_baseline(mats):
+    """Oracle GSE-SpMV (single thread) on a bounded sample: one pass at k = 1, 2, 3
+    over the 128^3 matrix."""
+    import oracle
+    oracle.build()
+    name, A = mats[0]
+    x = synth.uniform_x(A.n_cols, seed=0)
+    enc = oracle.encode(A.val)
+    t0 = time.perf_counter()
+    nbytes = 0.0
+    for k in (1, 2, 3):
+        oracle.gse_spmv(A.row_ptr, A.col, enc, k, x)
+        nbytes += algorithmic_bytes(A.nnz, A.n_rows, A.n_cols, k)
+    dt = time.perf_counter() - t0
+    return {"value": round(nbytes / dt / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"GSE-SpMV k=1,2,3 once over {name} ({A.nnz} nnz), {dt:.2f} s"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gse")
+    ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import paper_2411_04686_gb300 as gse
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    hbm_peak, peak_kind = load_peaks()
+    stream = torch.cuda.current_stream()
+
+    mats = build_workload()
+    handles = []
+    for name, A in mats:
+        M = gse.GseMatrix.from_csr(A, attach=(64, 32))
+        M.autotune(1)
+        x = torch.from_numpy(synth.uniform_x(A.n_cols, seed=0)).cuda()
+        y = torch.empty(A.n_rows, dtype=torch.float64, device="cuda")
+        handles.append((name, A, M, x, y))
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(6)]
+    launches = [(hi, k) for hi in range(len(handles)) for k in (1, 2, 3)]
+
+    def step(record):
+        times = []
+        for li, (hi, k) in enumerate(launches):
+            name, A, M, x, y = handles[hi]
+            flush.fill_(float(li))
+            e0, e1 = ev[li]
+            e0.record(stream)
+            M.spmv(k, x, y)
+            e1.record(stream)
+        if record:
+            torch.cuda.synchronize()
+            times = [ev[i][0].elapsed_time(ev[i][1]) for i in range(len(launches))]
+        return times
+
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    per_launch = [[] for _ in launches]
+    with Clocks(local) as clk:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ts = step(True)
+            for i, t in enumerate(ts):
+                per_launch[i].append(t)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    clocks = clk.summary()
+    kernel_ms = [sum(v) / len(v) for v in per_launch]
+    ms_step = sum(kernel_ms)
+    if dist:
+        t = torch.tensor([ms_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    bytes_step = sum(algorithmic_bytes(handles[hi][1].nnz, handles[hi][1].n_rows, handles[hi][1].n_cols, k)
+                     for hi, k in launches)
+    value = bytes_step * world / (ms_step * 1e-3) / 1e9
+
+    # per-k table and the dominant kernel's roofline
+    per_k = {}
+    for i, (hi, k) in enumerate(launches):
+        name, A = handles[hi][0], handles[hi][1]
+        nb = algorithmic_bytes(A.nnz, A.n_rows, A.n_cols, k)
+        gbs = nb / (kernel_ms[i] * 1e-3) / 1e9
+        dfma_bound_gbs = nb / (A.nnz / DFMA_PEAK_PER_S) / 1e9
+        per_k[f"{name}_k{k}"] = {"us": round(kernel_ms[i] * 1e3, 2), "GB_s": round(gbs, 1),
+                                 "frac_hbm_measured": round(gbs / hbm_peak, 3),
+                                 "frac_hbm_nominal_8TBs": round(gbs / 8000.0, 3),
+                                 "algorithmic_MB": round(nb / 1e6, 1),
+                                 "fp64_fma_bound_GB_s": round(dfma_bound_gbs, 1),
+                                 "bound": "hbm" if dfma_bound_gbs >= hbm_peak else "alu(fp64 fma)"}
+    dom = max(range(len(launches)), key=lambda i: kernel_ms[i])
+    hi, k = launches[dom]
+    dA = handles[hi][1]
+    dbytes = algorithmic_bytes(dA.nnz, dA.n_rows, dA.n_cols, k)
+    achieved = dbytes / (kernel_ms[dom] * 1e-3) / 1e9
+    traffic = None
+    tp = os.path.join(ROOT, "profiles", "spmv_traffic.json")
+    if os.path.exists(tp):
+        t = json.load(open(tp))
+        key = f"{handles[hi][0]}_k{k}"
+        if t.get("src_hash") == src_hash() and key in t.get("traffic_bytes", {}):
+            traffic = t["traffic_bytes"][key]
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(achieved / hbm_peak, 3), "traffic": traffic,
+                "kernel": f"k_spmv k={k} on {handles[hi][0]}", "peak_kind": peak_kind,
+                "algorithmic_bytes": int(dbytes)}
+
+    # baselines (not part of the step)
+    baselines = {}
+    for name, A, M, x, y in handles:
+        for lv, vb in ((gse.LEVEL_FP64, 8), (gse.LEVEL_FP32, 4)):
+            ts = []
+            for _ in range(10):
+                flush.fill_(1.0)
+                e0, e1 = ev[0]
+                e0.record(stream)
+                M.spmv(lv, x, y)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            ms = statistics.median(ts)
+            nb = csr_bytes(A.nnz, A.n_rows, A.n_cols, vb)
+            baselines[f"{name}_fp{lv}"] = {"us": round(ms * 1e3, 2), "GB_s": round(nb / (ms * 1e-3) / 1e9, 1),
+                                          "frac_hbm_measured": round(nb / (ms * 1e-3) / 1e9 / hbm_peak, 3)}
+        gse_k1 = per_k[f"{name}_k1"]["us"]
+        baselines[f"{name}_speedup_k1_vs_fp64"] = round(baselines[f"{name}_fp64"]["us"] / gse_k1, 3)
+
+    # e2e: through the C ABI with host buffers, copies inside the timed region
+    pinned_x = [torch.from_numpy(synth.uniform_x(h[1].n_cols, seed=0)).pin_memory() for h in handles]
+    pinned_y = [torch.empty(h[1].n_rows, dtype=torch.float64).pin_memory() for h in handles]
+    h2d = sum(p.numel() * 8 for p in pinned_x)
+    d2h = sum(3 * p.numel() * 8 for p in pinned_y)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    E = max(3, args.steps // 2)
+    for _ in range(E):
+        for hi, (name, A, M, x, y) in enumerate(handles):
+            x.copy_(pinned_x[hi], non_blocking=True)
+            for k in (1, 2, 3):
+                M.spmv(k, x, y)
+                pinned_y[hi].copy_(y, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / E
+    e2e = {"value": round(bytes_step * world / e2e_s / 1e9, 2), "unit": "GB/s",
+           "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    solve = None
+    if not args.no_solve:
+        solve = solver_comparison(gse, torch)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline(mats)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded; stand-ins for the paper's SuiteSparse sets)",
+            "config": {"workload": "gse_spmv_sweep_laplace3d128_powerlaw1m", "levels": [1, 2, 3],
+                       "group_size": 32, "seg_bits": [16, 16, 20], "l2": "flushed (256 MiB write) before each SpMV",
+                       "parallelism": "replicas" if world > 1 else "single_gpu",
+                       "wall_s_timed_region": round(wall, 3)},
+            "roofline": roofline, "per_k": per_k, "baselines": baselines, "solve": solve,
+            "e2e": e2e, "gpu_launches": len(launches) * args.steps, "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def solver_comparison(gse, torch):
+    """Time-to-1e-10: stepped GSE-CG vs FP64 CSR CG (same fused engine), on the
+    3D 7-point Laplacian 192^3 with diagonal shift 1e-3; b = A*1, x0 = 0."""
+    A = synth.laplace3d(192, shift=1e-3)
+    M = gse.GseMatrix.from_csr(A, attach=(64,))
+    b = torch.from_numpy(synth.rhs_ones(A)).cuda()
+    out = {"workload": "laplace3d_192_shift1e-3_cg_tol1e-10", "n": A.n_rows, "nnz": A.nnz}
+    variants = [("fp64_csr_cg", gse.fp64_policy(gse.SCALED_CG)),
+                ("gse_stepped_cg_paper_policy", gse.SCALED_CG),
+                ("gse_stepped_cg_floor_policy", gse.Policy(**{**gse.SCALED_CG.__dict__, "flags": gse.POLICY_FLOOR}))]
+    for name, pol in variants:
+        x = torch.zeros(A.n_rows, dtype=torch.float64, device="cuda")
+        M.cg(b, x, tol=1e-10, policy=pol)     # warm (workspace, floor coefficients)
+        x.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info = M.cg(b, x, tol=1e-10, policy=pol)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        err = float((x - 1.0).abs().max().item())
+        out[name] = {"seconds": round(dt, 4), "iters": info["iters"], "status": info["status"],
+                     "k_final": info["k_final"], "switch_iter": info["switch_iter"],
+                     "rel_res_true": info["rel_res_true"], "max_abs_err_vs_ones": err}
+    f = out["fp64_csr_cg"]["seconds"]
+    for name in ("gse_stepped_cg_paper_policy", "gse_stepped_cg_floor_policy"):
+        out[name]["speedup_vs_fp64"] = round(f / out[name]["seconds"], 3)
+    M.free()
+    return out
+
+
+if __name__ == "__main__":
+    main()

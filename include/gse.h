@@ -1,0 +1,225 @@
+/*
+ * gse.h -- C ABI of the GB300 library for group-shared-exponent (GSE) sparse
+ * matrices: encoding, SpMV at precision level k, and the stepped
+ * mixed-precision CG / GMRES solvers of "Precision-Aware Iterative Algorithms
+ * Based on Group-Shared Exponents of Floating-Point Numbers" (Gao et al.,
+ * arXiv 2411.04686).
+ *
+ * Conventions shared by every call:
+ *  - Every function returns an int status: GSE_OK (0), a positive solver
+ *    outcome (GSE_MAXITER, GSE_BREAKDOWN, GSE_NONFINITE, GSE_TIMEOUT) or a
+ *    negative error.  gse_strerror() names it.  No C++ exception crosses the ABI.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Work is enqueued on it; calls that return host data synchronise it.
+ *  - Vector arguments (x, y, b) are DEVICE pointers to contiguous FP64 arrays
+ *    owned by the caller, unless a parameter says otherwise.
+ *  - A handle owns all device memory it allocates.  Calls on one handle must
+ *    not overlap in time (the SpMV keeps per-handle scratch for rows that span
+ *    work chunks); distinct handles are independent.
+ *  - Matrix limits: nnz < 2^31, n_rows < 2^31, column indices in int32.
+ */
+#ifndef GSE_H
+#define GSE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define GSE_OK              0
+#define GSE_MAXITER         1   /* solve stopped at max_iter; info is filled      */
+#define GSE_BREAKDOWN       2   /* p.Ap <= 0 at k_max (CG) or a singular Hessenberg */
+#define GSE_NONFINITE       3   /* a solver scalar became Inf/NaN                 */
+#define GSE_TIMEOUT         4   /* a bounded device-side wait gave up             */
+#define GSE_ERR_INVALID    -1   /* bad argument or malformed CSR                  */
+#define GSE_ERR_NONFINITE  -2   /* encode input holds Inf/NaN                     */
+#define GSE_ERR_OOM        -3   /* device allocation failed                       */
+#define GSE_ERR_CUDA       -4   /* a CUDA runtime call failed                     */
+#define GSE_ERR_UNSUPPORTED -5  /* parameter outside what the kernels implement  */
+
+/* Level selectors beyond the GSE levels 1..n_seg: the plain CSR baselines
+ * (values attached with gse_attach_values). */
+#define GSE_LEVEL_FP64     64
+#define GSE_LEVEL_FP32     32
+
+/* Step-policy flags. */
+#define GSE_POLICY_NO_STAGNATION 1  /* never evaluate Conditions 1-3              */
+#define GSE_POLICY_FLOOR         2  /* also step when the recurrence residual falls
+                                       below the level's perturbation floor
+                                       (an addition beyond the paper)             */
+
+typedef struct gse_matrix* gse_handle;
+
+/* Input CSR (Sec. III-C, "Sparse Matrix Representation"): RowPtr, ColIdx, Val.
+ * Columns must be sorted within each row.  The caller keeps ownership; the
+ * arrays are copied.  on_device != 0 means the three pointers are device
+ * pointers, else host pointers. */
+typedef struct {
+    int64_t n_rows, n_cols, nnz;
+    const int32_t* row_ptr;
+    const int32_t* col_idx;
+    const double* val;
+    int on_device;
+} gse_csr;
+
+/* Parameters of the precision-step policy (Sec. III-D; values used in the
+ * paper are listed in Sec. IV-D).  l: iterations before the first check;
+ * t: history window; m: check period; rsd_limit / ndec_limit / reldec_limit:
+ * thresholds of Conditions 1-3 (ndec_limit <= 0 means t/2); max_iter: total
+ * iteration cap; restart: GMRES cycle length (<= 64); k_start / k_max: first and
+ * last precision level (1..n_seg, or GSE_LEVEL_FP64 / GSE_LEVEL_FP32 for both to
+ * run the plain CSR baseline); flags: GSE_POLICY_*. */
+typedef struct {
+    int l, t, m;
+    double rsd_limit;
+    int ndec_limit;
+    double reldec_limit;
+    int max_iter, restart, k_start, k_max, flags;
+} gse_step_policy;
+
+/* Outcome of a solve.  switch_iter[i]: iteration at which level i+1 became
+ * active (-1 if never).  rel_res_rec: last recurrence residual / ||b||;
+ * rel_res_true: ||b - A_kmax x|| / ||b|| recomputed at the end; seconds: wall
+ * time from entry to return. */
+typedef struct {
+    int status, iters, k_final;
+    int switch_iter[3];
+    double rel_res_rec, rel_res_true;
+    double seconds;
+} gse_solve_info;
+
+/* Static description of an encoded matrix. */
+typedef struct {
+    int64_t n_rows, n_cols, nnz, n_groups, n_empty_rows;
+    int group_size, n_seg, seg_bits[3];
+    int max_row_len;
+    double mean_row_len;
+    int schedule;                 /* nonzeros per lane-unit chunk: 1, 2 or 4 units */
+    int64_t bytes_level[3];       /* algorithmic bytes read+written by one SpMV   */
+} gse_matrix_info;
+
+/* Error name for a status code (static string). */
+const char* gse_strerror(int status);
+
+/*
+ * Encode a CSR matrix in the group-shared-exponent format (Sec. III-B, Alg. 1,
+ * Fig. 3), one shared exponent per group of `group_size` consecutive nonzeros
+ * in CSR order (groups may straddle rows; the last one may be partial):
+ *   E_g = max biased exponent in the group + 1 (0 for an all-zero group);
+ *   M   = floor(|v| * 2^(W - (E_g - 1023))), W = (s1 - 1) + s2 + s3;
+ *   head = sign << (s1-1) | top s1-1 bits of M; tail1 = next s2 bits;
+ *   tail2 = last s3 bits.
+ * group_size: 8, 16 or 32.  seg_bits[0..n_seg-1]: s1 in [2,16] (includes the
+ * sign), s2 in [1,16], s3 in [1,16] or {20, 24, 32}.  n_seg in 1..3.
+ * Also builds the row-end mask and chunk metadata the SpMV needs, measures
+ * row-length statistics and picks a schedule.
+ * Errors: GSE_ERR_INVALID (bad sizes, row_ptr not monotone, column out of
+ * range), GSE_ERR_NONFINITE (Inf/NaN value), GSE_ERR_UNSUPPORTED, GSE_ERR_OOM.
+ * On success *out owns everything; release with gse_free.
+ */
+int gse_encode(const gse_csr* csr, int group_size, const int* seg_bits, int n_seg,
+               void* stream, gse_handle* out);
+
+/* Attach plain CSR values to a handle for the FP64 (bits = 64) or FP32
+ * (bits = 32, rounded to nearest) baseline SpMV and solvers.  csr must have the
+ * structure the handle was encoded from. */
+int gse_attach_values(gse_handle h, const gse_csr* csr, int bits, void* stream);
+
+/*
+ * y = A_k x (Sec. III-C, Alg. 2 and the two tail variants): A_k is rebuilt
+ * from the first k segments (M_k = M >> (W - W_k), value = +-M_k *
+ * 2^(E_g - 1023 - W_k)), multiplied and accumulated in FP64.  k in 1..n_seg,
+ * or GSE_LEVEL_FP64 / GSE_LEVEL_FP32 for the attached baseline values.
+ * x: n_cols doubles, y: n_rows doubles (device, must not alias).
+ * Errors: GSE_ERR_INVALID (k out of range, NULL pointers).
+ */
+int gse_spmv(gse_handle h, int k, const double* x, double* y, void* stream);
+
+/*
+ * Stepped mixed-precision CG (Alg. 3 with the step policy of Sec. III-D,
+ * Eqs. 3-6, Conditions 1-3; FP64 vector operations as in Sec. IV-D).
+ * Starts at k_start; at a step the level rises by one, the residual is
+ * recomputed as b - A_k x and the search direction restarts.  When the
+ * recurrence residual falls below tol, the true residual with A_kmax decides:
+ * below tol ends the solve, otherwise the level steps (or, at k_max, the
+ * recurrence restarts from the true residual).
+ * b: n_rows doubles; x: initial guess in, solution out (device).  info may be
+ * NULL.  Returns GSE_OK, GSE_MAXITER, GSE_BREAKDOWN, GSE_NONFINITE or an error.
+ */
+int gse_cg(gse_handle h, const double* b, double* x, double tol, const gse_step_policy* policy,
+           gse_solve_info* info, void* stream);
+
+/*
+ * Stepped mixed-precision restarted GMRES(restart) (Alg. 3, Sec. III-D;
+ * FP64 modified Gram-Schmidt Arnoldi and Givens rotations on the device).  The
+ * level changes only at cycle boundaries; the monitored residual is the
+ * least-squares residual of each inner iteration.  Arguments as gse_cg.
+ */
+int gse_gmres(gse_handle h, const double* b, double* x, double tol, const gse_step_policy* policy,
+              gse_solve_info* info, void* stream);
+
+/*
+ * Batched stepped CG: nsys independent systems (each with its own handle,
+ * right-hand side and initial guess) solved concurrently, their kernels
+ * interleaved on one stream.  infos: nsys entries (may be NULL).  b and x are
+ * host arrays of nsys device pointers.  Returns the first non-OK status.
+ */
+int gse_batch_cg(int nsys, const gse_handle* hs, const double* const* b, double* const* x,
+                 double tol, const gse_step_policy* policy, gse_solve_info* infos, void* stream);
+
+/*
+ * Continuous-batching CG engine: the batched solver above, exposed step by
+ * step so that systems can join and leave while others run (serving).  Each
+ * submitted system occupies a slot; gse_engine_run advances every active
+ * system by up to max_slots iteration slots (one slot = one CG iteration, or
+ * one restart / true-residual step) with one set of kernel launches per slot
+ * for all of them; gse_engine_poll hands back finished systems and frees their
+ * slots.  A handle may occupy at most one slot at a time (its workspace holds
+ * the Krylov vectors).  Results of a system do not depend on what else runs.
+ */
+typedef struct gse_cg_engine* gse_engine;
+int gse_engine_create(int capacity, void* stream, gse_engine* out);
+int gse_engine_submit(gse_engine e, gse_handle h, const double* b, double* x, double tol,
+                      const gse_step_policy* policy, int* slot);
+int gse_engine_run(gse_engine e, int max_slots, int batch, int* n_running);
+int gse_engine_poll(gse_engine e, int* done_slots, gse_solve_info* infos, int max_done, int* n_done);
+int gse_engine_cancel(gse_engine e, int slot, gse_solve_info* info);
+void gse_engine_destroy(gse_engine e);
+
+/* Host copies of the logical segments (tests): head[nnz], tail1[nnz],
+ * tail2[nnz] (the s3-bit field, widened to 32 bits), gexp[n_groups].  Any
+ * pointer may be NULL to skip that array.  Synchronises the handle's stream. */
+int gse_export(gse_handle h, uint16_t* head, uint16_t* tail1, uint32_t* tail2, int16_t* gexp);
+
+/* vals[nnz] (device) = the FP64 values of A_k in CSR order (tests). */
+int gse_decode(gse_handle h, int k, double* vals, void* stream);
+
+/* Describes the handle. */
+int gse_matrix_get_info(gse_handle h, gse_matrix_info* info);
+
+/* Force the SpMV schedule (units of 8 nonzeros per lane: 1, 2 or 4); 0 restores
+ * the automatic choice. */
+int gse_set_schedule(gse_handle h, int units_per_lane);
+
+/* Time each schedule on this matrix at level k (CUDA events, a few reps) and
+ * keep the fastest. */
+int gse_autotune(gse_handle h, int k, void* stream);
+
+/* Device bytes held by the handle, solver workspace included. */
+size_t gse_footprint(gse_handle h);
+
+/* Device bytes a CG (method 0) or GMRES (method 1) solve of this handle will
+ * hold in total, encoded matrix included (admission control). */
+size_t gse_solve_footprint(gse_handle h, int method, int restart);
+
+/* Releases the handle and all its device memory (NULL is a no-op). */
+void gse_free(gse_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GSE_H */

@@ -1,0 +1,590 @@
+// encode.cu -- gse_encode (Sec. III-B, Alg. 1, Fig. 3) and the handle's life
+// cycle: validation, the group-shared-exponent encoder, row-end mask and chunk
+// metadata, row statistics, baseline values, export/decode, footprint.
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "spmv_core.cuh"
+
+namespace gse {
+
+// ---- validation -------------------------------------------------------------
+
+__global__ void k_validate_rows(const int32_t* row_ptr, int64_t n, int64_t nnz, int* err,
+                                int* max_len) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t s = row_ptr[r], t = row_ptr[r + 1];
+        if (t < s || s < 0 || t > nnz) atomicOr(err, 1);
+        else atomicMax(max_len, t - s);
+        if (r == 0 && s != 0) atomicOr(err, 1);
+        if (r == n - 1 && t != nnz) atomicOr(err, 1);
+    }
+}
+
+__global__ void k_validate_cols(const int32_t* col, int64_t nnz, int64_t n_cols, int* err) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t c = col[e];
+        if (c < 0 || c >= n_cols) atomicOr(err, 1);
+    }
+}
+
+// ---- the encoder ------------------------------------------------------------
+// One thread per nonzero; a warp covers 32 consecutive nonzeros, i.e. 32/G
+// whole groups.  Per group: E_g = max biased exponent + 1 (0 if all are zero
+// or subnormal); per value: M = floor(|v| 2^(W - (E_g - 1023))) (round toward
+// zero, as Alg. 1), then the head / tail1 / tail2 fields of Fig. 3.
+
+struct EncParams {
+    int G, s1, s2, s3, s3hi, r_lo, W, W1, W2, n_seg;
+};
+
+__global__ void k_encode(const double* __restrict__ val, const int32_t* __restrict__ col_in,
+                         int64_t nnz, int64_t nnz_pad, EncParams p, int32_t* col, uint16_t* head,
+                         uint16_t* tail1, uint16_t* t2hi, uint32_t* t2lo, uint16_t* gexp, int* err) {
+    const unsigned FULL = 0xFFFFFFFFu;
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz_pad; e += stride) {
+        const bool real = e < nnz;
+        const uint64_t b = real ? (uint64_t)__double_as_longlong(val[e]) : 0ull;
+        const int ex = (int)((b >> 52) & 0x7FF);
+        if (ex == 0x7FF) atomicOr(err, 2);
+        int emax = ex;
+        for (int o = 1; o < p.G; o <<= 1) emax = max(emax, __shfl_xor_sync(FULL, emax, o));
+        const int Eg = emax == 0 ? 0 : emax + 1;
+        uint64_t M = 0;
+        if (ex != 0 && ex != 0x7FF) {
+            const uint64_t S = (1ull << 52) | (b & 0xFFFFFFFFFFFFFull);
+            const int sh = p.W - 52 - (Eg - ex);
+            M = sh >= 0 ? (S << sh) : (-sh < 64 ? (S >> (-sh)) : 0ull);
+        }
+        const uint32_t sign = (uint32_t)(b >> 63);
+        head[e] = (uint16_t)((sign << (p.s1 - 1)) | (uint32_t)(M >> (p.W - p.W1)));
+        if (p.n_seg >= 2) tail1[e] = (uint16_t)((M >> (p.W - p.W2)) & ((1ull << p.s2) - 1));
+        if (p.n_seg >= 3) {
+            const uint32_t t2 = (uint32_t)(M & ((1ull << p.s3) - 1));
+            t2hi[e] = (uint16_t)(t2 >> p.r_lo);
+            if (p.r_lo > 0) {
+                const int i = (int)(e & 7);
+                const int bit = i * p.r_lo;
+                uint32_t w = (t2 & ((1u << p.r_lo) - 1u)) << (bit & 31);
+                const int lanes_per_word = 32 / p.r_lo;
+                for (int o = 1; o < lanes_per_word; o <<= 1) w |= __shfl_xor_sync(FULL, w, o);
+                if ((i % lanes_per_word) == 0)
+                    t2lo[(e >> 3) * (p.r_lo / 4) + (bit >> 5)] = w;
+            }
+        }
+        if ((lane & (p.G - 1)) == 0) gexp[e / p.G] = (uint16_t)Eg;
+        col[e] = real ? col_in[e] : 0;
+    }
+}
+
+// ---- structure metadata -----------------------------------------------------
+
+__global__ void k_rowend(const int32_t* row_ptr, int64_t n, uint32_t* rowend, int* flag_nonempty,
+                         int* flag_empty) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t s = row_ptr[r], t = row_ptr[r + 1];
+        if (t > s) atomicOr(rowend + ((t - 1) >> 5), 1u << ((t - 1) & 31));
+        flag_nonempty[r] = t > s;
+        flag_empty[r] = t == s;
+    }
+}
+
+__global__ void k_block_popc(const uint32_t* rowend, int64_t nblk, int* out) {
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nblk; b += (int64_t)gridDim.x * blockDim.x) {
+        int s = 0;
+        for (int i = 0; i < 8; i++) s += __popc(rowend[b * 8 + i]);
+        out[b] = s;
+    }
+}
+
+// Exclusive scan of int32 (three passes: block sums, scan of the sums, apply).
+constexpr int SCAN_BLOCK = 1024;
+constexpr int SCAN_ITEMS = 4;
+constexpr int SCAN_TILE = SCAN_BLOCK * SCAN_ITEMS;
+
+__device__ int block_exclusive_scan(int v, int* sh, int* total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    __syncthreads();
+    if (lane == 31) sh[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        const int nw = blockDim.x >> 5;
+        int x = lane < nw ? sh[lane] : 0;
+        int xi = x;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xFFFFFFFFu, xi, o);
+            if (lane >= o) xi += t;
+        }
+        if (lane < nw) sh[lane] = xi - x;
+        if (lane == 31) sh[32] = xi;
+    }
+    __syncthreads();
+    const int res = incl - v + sh[w];
+    if (total) *total = sh[32];
+    return res;
+}
+
+__global__ void k_scan_reduce(const int* in, int64_t n, int* bsum) {
+    __shared__ int sh[33];
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+    int s = 0;
+    for (int i = 0; i < SCAN_ITEMS; i++) {
+        const int64_t idx = base + (int64_t)threadIdx.x * SCAN_ITEMS + i;
+        if (idx < n) s += in[idx];
+    }
+    int total;
+    block_exclusive_scan(s, sh, &total);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = total;
+}
+
+__global__ void k_scan_bsum(int* bsum, int64_t nb, int* grand_total) {
+    __shared__ int sh[33];
+    int carry = 0;
+    for (int64_t base = 0; base < nb; base += blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        const int v = i < nb ? bsum[i] : 0;
+        int total;
+        const int ex = block_exclusive_scan(v, sh, &total);
+        if (i < nb) bsum[i] = ex + carry;
+        carry += total;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *grand_total = carry;
+}
+
+__global__ void k_scan_apply(const int* in, int64_t n, const int* bsum, int* out) {
+    __shared__ int sh[33];
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+    int v[SCAN_ITEMS];
+    int s = 0;
+    for (int i = 0; i < SCAN_ITEMS; i++) {
+        const int64_t idx = base + (int64_t)threadIdx.x * SCAN_ITEMS + i;
+        v[i] = idx < n ? in[idx] : 0;
+        s += v[i];
+    }
+    int ex = block_exclusive_scan(s, sh, nullptr) + bsum[blockIdx.x];
+    for (int i = 0; i < SCAN_ITEMS; i++) {
+        const int64_t idx = base + (int64_t)threadIdx.x * SCAN_ITEMS + i;
+        if (idx < n) out[idx] = ex;
+        ex += v[i];
+    }
+}
+
+// out[i] = exclusive prefix of in[0..i); *total (device) = sum.  tmp: ceil(n/TILE) ints.
+static void exclusive_scan(const int* in, int64_t n, int* out, int* tmp, int* total, cudaStream_t s) {
+    const int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+    if (nb > 0) {
+        k_scan_reduce<<<(unsigned)nb, SCAN_BLOCK, 0, s>>>(in, n, tmp);
+        k_scan_bsum<<<1, SCAN_BLOCK, 0, s>>>(tmp, nb, total);
+        k_scan_apply<<<(unsigned)nb, SCAN_BLOCK, 0, s>>>(in, n, tmp, out);
+    } else {
+        cudaMemsetAsync(total, 0, sizeof(int), s);
+    }
+}
+
+__global__ void k_scatter_rows(const int* flag, const int* pos, int64_t n, int32_t* dst) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+        if (flag[r]) dst[pos[r]] = (int32_t)r;
+}
+
+__global__ void k_pad_values(const double* val, int64_t nnz, int64_t nnz_pad, double* v64, float* v32) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz_pad; e += (int64_t)gridDim.x * blockDim.x) {
+        const double v = e < nnz ? val[e] : 0.0;
+        if (v64) v64[e] = v;
+        if (v32) v32[e] = __double2float_rn(v);
+    }
+}
+
+template <int K, int R>
+__global__ void k_decode(MatView m, double* out) {
+    const int64_t nunits = (m.nnz + 7) / 8;
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < nunits; u += (int64_t)gridDim.x * blockDim.x) {
+        int col[8];
+        double a[8];
+        load_unit<K, R>(m, u, col, a);
+        for (int i = 0; i < 8; i++)
+            if (u * 8 + i < m.nnz) out[u * 8 + i] = a[i];
+    }
+}
+
+static unsigned grid_for(int64_t n, int threads = 256) {
+    int64_t g = (n + threads - 1) / threads;
+    if (g > 65535LL * 16) g = 65535LL * 16;
+    if (g < 1) g = 1;
+    return (unsigned)g;
+}
+
+static void free_all(gse_matrix* h) {
+    void* bufs[] = {h->buf_col, h->buf_head, h->buf_tail1, h->buf_t2hi, h->buf_t2lo, h->buf_gexp,
+                    h->buf_rowend, h->buf_blk_row0, h->buf_nzrow, h->buf_empty, h->buf_row_ptr,
+                    h->buf_val64, h->buf_val32, h->buf_carry, h->buf_part, h->buf_cnt,
+                    h->red_partial, h->red_counter, h->red_result};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+}
+
+}  // namespace gse
+
+using namespace gse;
+
+void gse_free_workspace(gse_matrix* h);  // solver.cu
+
+extern "C" const char* gse_strerror(int status) {
+    switch (status) {
+        case GSE_OK: return "ok";
+        case GSE_MAXITER: return "maximum iterations reached";
+        case GSE_BREAKDOWN: return "solver breakdown";
+        case GSE_NONFINITE: return "non-finite value in the solver";
+        case GSE_TIMEOUT: return "bounded wait timed out";
+        case GSE_ERR_INVALID: return "invalid argument or malformed CSR";
+        case GSE_ERR_NONFINITE: return "input value is Inf or NaN";
+        case GSE_ERR_OOM: return "device allocation failed";
+        case GSE_ERR_CUDA: return "CUDA runtime error";
+        case GSE_ERR_UNSUPPORTED: return "unsupported parameter";
+        default: return "unknown status";
+    }
+}
+
+template <typename T>
+static int dev_alloc(T** p, size_t count, size_t* acc) {
+    if (count == 0) count = 1;
+    const size_t bytes = count * sizeof(T);
+    if (cudaMalloc((void**)p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return GSE_ERR_OOM;
+    }
+    *acc += bytes;
+    return GSE_OK;
+}
+
+static int encode_impl(const gse_csr* csr, int G, const int* seg_bits, int n_seg, cudaStream_t s,
+                       gse_matrix* h) {
+    const int64_t n = csr->n_rows, nnz = csr->nnz;
+    h->group_size = G;
+    h->n_seg = n_seg;
+    int sb[3] = {0, 0, 0};
+    for (int i = 0; i < n_seg; i++) sb[i] = seg_bits[i];
+    memcpy(h->seg_bits, sb, sizeof(sb));
+    MatView& v = h->v;
+    v.nnz = nnz;
+    v.n_rows = n;
+    v.n_cols = csr->n_cols;
+    v.nnz_pad = ((nnz + GSE_CHUNK_MAX - 1) / GSE_CHUNK_MAX) * GSE_CHUNK_MAX;
+    if (v.nnz_pad == 0) v.nnz_pad = GSE_CHUNK_MAX;
+    v.g_shift = G == 8 ? 3 : G == 16 ? 4 : 5;
+    v.s1 = sb[0];
+    v.s2 = n_seg >= 2 ? sb[1] : 0;
+    v.s3 = n_seg >= 3 ? sb[2] : 0;
+    v.s3hi = v.s3 > 16 ? 16 : v.s3;
+    v.r_lo = v.s3 - v.s3hi;
+    v.W1 = sb[0] - 1;
+    v.W2 = v.W1 + v.s2;
+    v.W3 = v.W2 + v.s3;
+    const int64_t npad = v.nnz_pad, nblk = npad / 256, ngroups = (nnz + G - 1) / G;
+    size_t acc = 0;
+    int rc;
+#define ALLOC(ptr, T, cnt) \
+    do { T* _p; if ((rc = dev_alloc(&_p, (size_t)(cnt), &acc)) != GSE_OK) return rc; ptr = _p; } while (0)
+    ALLOC(h->buf_row_ptr, int32_t, n + 1);
+    ALLOC(h->buf_col, int32_t, npad);
+    ALLOC(h->buf_head, uint16_t, npad);
+    if (n_seg >= 2) ALLOC(h->buf_tail1, uint16_t, npad);
+    if (n_seg >= 3) ALLOC(h->buf_t2hi, uint16_t, npad);
+    if (n_seg >= 3 && v.r_lo > 0) ALLOC(h->buf_t2lo, uint32_t, npad / 8 * v.r_lo / 4);
+    ALLOC(h->buf_gexp, uint16_t, npad / G);
+    ALLOC(h->buf_rowend, uint32_t, npad / 32);
+    ALLOC(h->buf_blk_row0, int32_t, nblk + 1);
+    ALLOC(h->buf_carry, double, nblk);
+    ALLOC(h->buf_part, double, nblk);
+    ALLOC(h->buf_cnt, int32_t, nblk);
+    h->red_capacity = h->num_sms * 32;
+    ALLOC(h->red_partial, double, h->red_capacity);
+    ALLOC(h->red_counter, unsigned, 4);
+    ALLOC(h->red_result, double, 4);
+    h->bytes_matrix = acc;
+    // temporaries
+    int *d_err = nullptr, *d_tmp = nullptr, *d_flag = nullptr, *d_flag2 = nullptr, *d_pos = nullptr;
+    int *d_scan_tmp = nullptr, *d_total = nullptr;
+    double* d_val = nullptr;
+    const int32_t* d_colin = nullptr;
+    int32_t* d_colin_own = nullptr;
+    size_t tacc = 0;
+    const int64_t nflags = n > nblk ? n : nblk;
+    if ((rc = dev_alloc(&d_err, 8, &tacc)) != GSE_OK) return rc;
+    bool ok = dev_alloc(&d_flag, nflags + 1, &tacc) == GSE_OK && dev_alloc(&d_flag2, nflags + 1, &tacc) == GSE_OK &&
+              dev_alloc(&d_pos, nflags + 1, &tacc) == GSE_OK &&
+              dev_alloc(&d_scan_tmp, nflags / SCAN_TILE + 2, &tacc) == GSE_OK &&
+              dev_alloc(&d_total, 4, &tacc) == GSE_OK;
+    if (ok && !csr->on_device) ok = dev_alloc(&d_val, nnz, &tacc) == GSE_OK && dev_alloc(&d_colin_own, nnz, &tacc) == GSE_OK;
+    (void)d_tmp;
+    int status = GSE_OK;
+    if (!ok) status = GSE_ERR_OOM;
+    if (status == GSE_OK) {
+        cudaMemsetAsync(d_err, 0, 8 * sizeof(int), s);
+        int32_t* rp = (int32_t*)h->buf_row_ptr;
+        if (csr->on_device) {
+            cudaMemcpyAsync(rp, csr->row_ptr, (n + 1) * sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
+            d_colin = csr->col_idx;
+        } else {
+            cudaMemcpyAsync(rp, csr->row_ptr, (n + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+            cudaMemcpyAsync(d_colin_own, csr->col_idx, nnz * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+            cudaMemcpyAsync(d_val, csr->val, nnz * sizeof(double), cudaMemcpyHostToDevice, s);
+            d_colin = d_colin_own;
+        }
+        const double* val = csr->on_device ? csr->val : d_val;
+        // validation
+        if (n > 0) k_validate_rows<<<grid_for(n), 256, 0, s>>>(rp, n, nnz, d_err, d_err + 1);
+        if (nnz > 0) k_validate_cols<<<grid_for(nnz), 256, 0, s>>>(d_colin, nnz, v.n_cols, d_err);
+        int herr[2] = {0, 0};
+        cudaMemcpyAsync(herr, d_err, 2 * sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess) status = GSE_ERR_CUDA;
+        else if (herr[0]) status = GSE_ERR_INVALID;
+        h->max_row_len = herr[1];
+        if (status == GSE_OK) {
+            EncParams p;
+            p.G = G;
+            p.s1 = v.s1;
+            p.s2 = v.s2;
+            p.s3 = v.s3;
+            p.s3hi = v.s3hi;
+            p.r_lo = v.r_lo;
+            p.W = n_seg == 1 ? v.W1 : n_seg == 2 ? v.W2 : v.W3;
+            p.W1 = v.W1;
+            p.W2 = v.W2;
+            p.n_seg = n_seg;
+            k_encode<<<grid_for(npad), 256, 0, s>>>(val, d_colin, nnz, npad, p, (int32_t*)h->buf_col,
+                                                    (uint16_t*)h->buf_head, (uint16_t*)h->buf_tail1,
+                                                    (uint16_t*)h->buf_t2hi, (uint32_t*)h->buf_t2lo,
+                                                    (uint16_t*)h->buf_gexp, d_err);
+            // row ends, empty rows
+            cudaMemsetAsync(h->buf_rowend, 0, npad / 32 * sizeof(uint32_t), s);
+            if (n > 0) k_rowend<<<grid_for(n), 256, 0, s>>>(rp, n, (uint32_t*)h->buf_rowend, d_flag, d_flag2);
+            exclusive_scan(d_flag, n, d_pos, d_scan_tmp, d_total, s);
+            int n_nonempty = 0;
+            cudaMemcpyAsync(&n_nonempty, d_total, sizeof(int), cudaMemcpyDeviceToHost, s);
+            cudaMemcpyAsync(herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
+            if (cudaStreamSynchronize(s) != cudaSuccess) status = GSE_ERR_CUDA;
+            else if (herr[0] & 2) status = GSE_ERR_NONFINITE;
+            v.n_nonempty = n_nonempty;
+            v.n_empty = n - n_nonempty;
+            if (status == GSE_OK && v.n_empty > 0) {
+                int32_t *nz, *em;
+                if (dev_alloc(&nz, (size_t)n_nonempty, &h->bytes_matrix) != GSE_OK ||
+                    (h->buf_nzrow = nz, dev_alloc(&em, (size_t)v.n_empty, &h->bytes_matrix)) != GSE_OK) {
+                    status = GSE_ERR_OOM;
+                } else {
+                    h->buf_empty = em;
+                    k_scatter_rows<<<grid_for(n), 256, 0, s>>>(d_flag, d_pos, n, nz);
+                    exclusive_scan(d_flag2, n, d_pos, d_scan_tmp, d_total, s);
+                    k_scatter_rows<<<grid_for(n), 256, 0, s>>>(d_flag2, d_pos, n, em);
+                }
+            }
+            if (status == GSE_OK) {
+                k_block_popc<<<grid_for(nblk), 256, 0, s>>>((uint32_t*)h->buf_rowend, nblk, d_flag);
+                exclusive_scan(d_flag, nblk, (int*)h->buf_blk_row0, d_scan_tmp, d_total, s);
+                cudaMemsetAsync(h->buf_cnt, 0, nblk * sizeof(int32_t), s);
+                cudaMemsetAsync(h->red_counter, 0, 4 * sizeof(unsigned), s);
+                if (cudaStreamSynchronize(s) != cudaSuccess) status = GSE_ERR_CUDA;
+            }
+        }
+    }
+    cudaFree(d_err);
+    if (d_flag) cudaFree(d_flag);
+    if (d_flag2) cudaFree(d_flag2);
+    if (d_pos) cudaFree(d_pos);
+    if (d_scan_tmp) cudaFree(d_scan_tmp);
+    if (d_total) cudaFree(d_total);
+    if (d_val) cudaFree(d_val);
+    if (d_colin_own) cudaFree(d_colin_own);
+    if (status != GSE_OK) return status;
+    v.col = (const int32_t*)h->buf_col;
+    v.head = (const uint16_t*)h->buf_head;
+    v.tail1 = (const uint16_t*)h->buf_tail1;
+    v.t2hi = (const uint16_t*)h->buf_t2hi;
+    v.t2lo = (const uint32_t*)h->buf_t2lo;
+    v.gexp = (const uint16_t*)h->buf_gexp;
+    v.rowend = (const uint32_t*)h->buf_rowend;
+    v.blk_row0 = (const int32_t*)h->buf_blk_row0;
+    v.nzrow = (const int32_t*)h->buf_nzrow;
+    v.empty = (const int32_t*)h->buf_empty;
+    v.row_ptr = (const int32_t*)h->buf_row_ptr;
+    v.carry = (double*)h->buf_carry;
+    v.part = (double*)h->buf_part;
+    v.cnt = (int32_t*)h->buf_cnt;
+    h->mean_row_len = n > 0 ? (double)nnz / (double)n : 0.0;
+    // schedule: short rows favour 1 unit of 8 per lane (fewer idle lanes per
+    // chunk), longer rows 2 (fewer chunk overheads)
+    h->schedule_auto = h->mean_row_len <= 10.0 ? 1 : 2;
+    h->schedule_forced = 0;
+    return GSE_OK;
+#undef ALLOC
+}
+
+extern "C" int gse_encode(const gse_csr* csr, int group_size, const int* seg_bits, int n_seg,
+                          void* stream, gse_handle* out) {
+    if (!csr || !seg_bits || !out) return GSE_ERR_INVALID;
+    *out = nullptr;
+    if (csr->n_rows < 0 || csr->n_cols < 0 || csr->nnz < 0 || csr->nnz >= (1LL << 31) ||
+        csr->n_rows >= (1LL << 31) || csr->n_cols >= (1LL << 31))
+        return GSE_ERR_INVALID;
+    if (!csr->row_ptr || (csr->nnz > 0 && (!csr->col_idx || !csr->val))) return GSE_ERR_INVALID;
+    if (n_seg < 1 || n_seg > 3) return GSE_ERR_INVALID;
+    if (seg_bits[0] < 2 || seg_bits[0] > 16) return GSE_ERR_INVALID;
+    if (n_seg >= 2 && (seg_bits[1] < 1 || seg_bits[1] > 16)) return GSE_ERR_INVALID;
+    if (n_seg >= 3) {
+        const int s3 = seg_bits[2];
+        if (s3 < 1 || s3 > 32) return GSE_ERR_INVALID;
+        if (s3 > 16 && s3 != 20 && s3 != 24 && s3 != 32) return GSE_ERR_UNSUPPORTED;
+    }
+    if (group_size != 8 && group_size != 16 && group_size != 32) return GSE_ERR_UNSUPPORTED;
+    gse_matrix* h = (gse_matrix*)calloc(1, sizeof(gse_matrix));
+    if (!h) return GSE_ERR_OOM;
+    cudaGetDevice(&h->device);
+    cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (h->num_sms < 1) h->num_sms = 1;
+    const int rc = encode_impl(csr, group_size, seg_bits, n_seg, (cudaStream_t)stream, h);
+    if (rc != GSE_OK) {
+        free_all(h);
+        free(h);
+        return rc;
+    }
+    *out = h;
+    return GSE_OK;
+}
+
+extern "C" int gse_attach_values(gse_handle h, const gse_csr* csr, int bits, void* stream) {
+    if (!h || !csr || (bits != 64 && bits != 32)) return GSE_ERR_INVALID;
+    if (csr->nnz != h->v.nnz || csr->n_rows != h->v.n_rows || (csr->nnz > 0 && !csr->val)) return GSE_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    const double* val = csr->val;
+    double* tmp = nullptr;
+    if (!csr->on_device) {
+        if (cudaMalloc(&tmp, (size_t)(h->v.nnz + 1) * sizeof(double)) != cudaSuccess) return GSE_ERR_OOM;
+        cudaMemcpyAsync(tmp, csr->val, h->v.nnz * sizeof(double), cudaMemcpyHostToDevice, s);
+        val = tmp;
+    }
+    double* v64 = nullptr;
+    float* v32 = nullptr;
+    int rc = GSE_OK;
+    if (bits == 64 && !h->buf_val64) rc = dev_alloc(&v64, (size_t)h->v.nnz_pad, &h->bytes_matrix);
+    if (bits == 32 && !h->buf_val32) rc = dev_alloc(&v32, (size_t)h->v.nnz_pad, &h->bytes_matrix);
+    if (rc == GSE_OK) {
+        if (v64) h->buf_val64 = v64;
+        if (v32) h->buf_val32 = v32;
+        k_pad_values<<<grid_for(h->v.nnz_pad), 256, 0, s>>>(val, h->v.nnz, h->v.nnz_pad,
+                                                            bits == 64 ? (double*)h->buf_val64 : nullptr,
+                                                            bits == 32 ? (float*)h->buf_val32 : nullptr);
+        h->v.val64 = (const double*)h->buf_val64;
+        h->v.val32 = (const float*)h->buf_val32;
+    }
+    if (tmp) {
+        cudaStreamSynchronize(s);
+        cudaFree(tmp);
+    }
+    if (cudaGetLastError() != cudaSuccess) return GSE_ERR_CUDA;
+    return rc;
+}
+
+extern "C" int gse_export(gse_handle h, uint16_t* head, uint16_t* tail1, uint32_t* tail2, int16_t* gexp) {
+    if (!h) return GSE_ERR_INVALID;
+    const int64_t nnz = h->v.nnz;
+    cudaDeviceSynchronize();
+    if (head && nnz) GSE_CUDA_TRY(cudaMemcpy(head, h->buf_head, nnz * sizeof(uint16_t), cudaMemcpyDeviceToHost));
+    if (tail1 && nnz) {
+        if (h->n_seg >= 2) GSE_CUDA_TRY(cudaMemcpy(tail1, h->buf_tail1, nnz * sizeof(uint16_t), cudaMemcpyDeviceToHost));
+        else memset(tail1, 0, nnz * sizeof(uint16_t));
+    }
+    if (tail2 && nnz) {
+        if (h->n_seg >= 3) {
+            std::vector<uint16_t> hi(nnz);
+            GSE_CUDA_TRY(cudaMemcpy(hi.data(), h->buf_t2hi, nnz * sizeof(uint16_t), cudaMemcpyDeviceToHost));
+            const int r = h->v.r_lo;
+            std::vector<uint32_t> lo;
+            if (r > 0) {
+                lo.resize(h->v.nnz_pad / 8 * r / 4);
+                GSE_CUDA_TRY(cudaMemcpy(lo.data(), h->buf_t2lo, lo.size() * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+            }
+            for (int64_t e = 0; e < nnz; e++) {
+                uint32_t t = hi[e];
+                if (r > 0) {
+                    const int bit = (int)(e & 7) * r;
+                    t = (t << r) | ((lo[(e >> 3) * (r / 4) + (bit >> 5)] >> (bit & 31)) & ((1u << r) - 1u));
+                }
+                tail2[e] = t;
+            }
+        } else {
+            memset(tail2, 0, nnz * sizeof(uint32_t));
+        }
+    }
+    const int64_t ng = (nnz + h->group_size - 1) / h->group_size;
+    if (gexp && ng) GSE_CUDA_TRY(cudaMemcpy(gexp, h->buf_gexp, ng * sizeof(int16_t), cudaMemcpyDeviceToHost));
+    return GSE_OK;
+}
+
+extern "C" int gse_decode(gse_handle h, int k, double* vals, void* stream) {
+    if (!h || !vals) return GSE_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t nunits = (h->v.nnz + 7) / 8;
+    const unsigned g = grid_for(nunits);
+    if (k == 1) k_decode<1, 0><<<g, 256, 0, s>>>(h->v, vals);
+    else if (k == 2 && h->n_seg >= 2) k_decode<2, 0><<<g, 256, 0, s>>>(h->v, vals);
+    else if (k == 3 && h->n_seg >= 3) {
+        switch (h->v.r_lo) {
+            case 0: k_decode<3, 0><<<g, 256, 0, s>>>(h->v, vals); break;
+            case 4: k_decode<3, 4><<<g, 256, 0, s>>>(h->v, vals); break;
+            case 8: k_decode<3, 8><<<g, 256, 0, s>>>(h->v, vals); break;
+            default: k_decode<3, 16><<<g, 256, 0, s>>>(h->v, vals); break;
+        }
+    } else if (k == GSE_LEVEL_FP64 && h->v.val64) k_decode<SRC_FP64, 0><<<g, 256, 0, s>>>(h->v, vals);
+    else if (k == GSE_LEVEL_FP32 && h->v.val32) k_decode<SRC_FP32, 0><<<g, 256, 0, s>>>(h->v, vals);
+    else return GSE_ERR_INVALID;
+    return cudaGetLastError() == cudaSuccess ? GSE_OK : GSE_ERR_CUDA;
+}
+
+extern "C" int gse_matrix_get_info(gse_handle h, gse_matrix_info* info) {
+    if (!h || !info) return GSE_ERR_INVALID;
+    memset(info, 0, sizeof(*info));
+    info->n_rows = h->v.n_rows;
+    info->n_cols = h->v.n_cols;
+    info->nnz = h->v.nnz;
+    info->n_groups = (h->v.nnz + h->group_size - 1) / h->group_size;
+    info->n_empty_rows = h->v.n_empty;
+    info->group_size = h->group_size;
+    info->n_seg = h->n_seg;
+    for (int i = 0; i < 3; i++) info->seg_bits[i] = h->seg_bits[i];
+    info->max_row_len = h->max_row_len;
+    info->mean_row_len = h->mean_row_len;
+    info->schedule = units_per_lane(h);
+    // algorithmic bytes: col + live segments + group exponent per nonzero,
+    // row_ptr, x read once, y written once
+    const double nnz = (double)h->v.nnz, n = (double)h->v.n_rows, nc = (double)h->v.n_cols;
+    const double base = nnz * 4.0 + nnz / h->group_size * 2.0 + 4.0 * (n + 1) + 8.0 * nc + 8.0 * n;
+    double seg = 0.0;
+    for (int k = 0; k < h->n_seg; k++) {
+        seg += nnz * h->seg_bits[k] / 8.0;
+        info->bytes_level[k] = (int64_t)(base + seg);
+    }
+    return GSE_OK;
+}
+
+extern "C" size_t gse_footprint(gse_handle h) {
+    if (!h) return 0;
+    return h->bytes_matrix + h->bytes_ws;
+}
+
+extern "C" void gse_free(gse_handle h) {
+    if (!h) return;
+    cudaDeviceSynchronize();
+    gse_free_workspace(h);
+    free_all(h);
+    free(h);
+}

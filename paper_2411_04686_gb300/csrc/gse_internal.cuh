@@ -1,0 +1,132 @@
+// gse_internal.cuh -- handle layout and helpers shared by the library's .cu files.
+//
+// Device layout of an encoded matrix (all arrays padded to nnz_pad, a multiple
+// of CHUNK_MAX = 1024 nonzeros, so every chunk of every schedule is full):
+//   col     int32[nnz_pad]            column indices (padding: 0)
+//   head    u16[nnz_pad]              sign | top W_1 magnitude bits
+//   tail1   u16[nnz_pad]              next s2 bits           (n_seg >= 2)
+//   t2hi    u16[nnz_pad]              top min(s3,16) bits of tail2 (n_seg = 3)
+//   t2lo    u32[nnz_pad / 8 * r / 4]  low r = s3 - 16 bits, packed per unit of
+//                                     8 nonzeros (r in {4, 8, 16}), r bytes each
+//   gexp    u16[n_groups]             group exponent E_g = max e + 1 (0: all zero)
+//   rowend  u32[nnz_pad / 32]         bit e: nonzero e is the last of its row
+//   blk_row0 int32[nnz_pad / 256]     compact index (nonempty rows only) of the
+//                                     row holding nonzero 256*b
+//   nzrow   int32[n_nonempty]         compact -> actual row (only with empty rows)
+//   empty   int32[n_empty]            the empty rows (zero-filled by every SpMV)
+// Split-row scratch (rows spanning chunks), indexed by 256-nonzero block:
+//   carry f64, part f64, cnt int32 (cnt zeroed once; every SpMV leaves it zero).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/gse.h"
+
+#define GSE_CHUNK_BASE 256   // nonzeros per lane-unit chunk with 1 unit per lane
+#define GSE_CHUNK_MAX 1024   // with 4 units per lane
+#define GSE_UNIT 8           // consecutive nonzeros per unit
+
+namespace gse {
+
+// Device-side view of an encoded matrix, passed to kernels by value.
+struct MatView {
+    const int32_t* col;
+    const uint16_t* head;
+    const uint16_t* tail1;
+    const uint16_t* t2hi;
+    const uint32_t* t2lo;
+    const uint16_t* gexp;
+    const uint32_t* rowend;
+    const int32_t* blk_row0;
+    const int32_t* nzrow;      // nullptr when every row is nonempty
+    const int32_t* empty;
+    const int32_t* row_ptr;
+    const double* val64;
+    const float* val32;
+    double* carry;
+    double* part;
+    int32_t* cnt;
+    int64_t nnz, nnz_pad, n_rows, n_cols, n_nonempty, n_empty;
+    int g_shift;               // log2(group size)
+    int s1, s2, s3, s3hi, r_lo; // segment widths; s3hi = min(s3,16), r_lo = s3 - s3hi
+    int W1, W2, W3;
+};
+
+struct Workspace;  // solver vectors, allocated on first solve (solver.cu)
+
+}  // namespace gse
+
+struct gse_matrix {
+    gse::MatView v;
+    int group_size;
+    int n_seg;
+    int seg_bits[3];
+    int max_row_len;
+    double mean_row_len;
+    int schedule_auto;   // units per lane chosen from row statistics / autotune
+    int schedule_forced; // 0: automatic
+    int num_sms;
+    int device;
+    // owned device allocations
+    void* buf_col;
+    void* buf_head;
+    void* buf_tail1;
+    void* buf_t2hi;
+    void* buf_t2lo;
+    void* buf_gexp;
+    void* buf_rowend;
+    void* buf_blk_row0;
+    void* buf_nzrow;
+    void* buf_empty;
+    void* buf_row_ptr;
+    void* buf_val64;
+    void* buf_val32;
+    void* buf_carry;
+    void* buf_part;
+    void* buf_cnt;
+    // small scratch for grid reductions
+    double* red_partial;   // one per block
+    unsigned* red_counter;
+    double* red_result;
+    int red_capacity;
+    size_t bytes_matrix;
+    gse::Workspace* ws;
+    size_t bytes_ws;
+};
+
+namespace gse {
+
+// Status helpers.
+#define GSE_CUDA_TRY(expr)                                  \
+    do {                                                    \
+        cudaError_t _e = (expr);                            \
+        if (_e != cudaSuccess) {                            \
+            if (_e == cudaErrorMemoryAllocation) return GSE_ERR_OOM; \
+            return GSE_ERR_CUDA;                            \
+        }                                                   \
+    } while (0)
+
+inline int units_per_lane(const gse_matrix* h) {
+    return h->schedule_forced ? h->schedule_forced : h->schedule_auto;
+}
+
+// SpMV launch (spmv.cu).  Epilogue kinds:
+enum EpiKind { EPI_STORE = 0, EPI_CG_PQ = 1, EPI_RESID = 2 };
+
+struct SpmvArgs {
+    const double* x;     // gathered vector
+    double* y;           // output (EPI_STORE / EPI_CG_PQ: y = A x; EPI_RESID: y = b - A x)
+    const double* b;     // EPI_RESID
+    const double* p;     // EPI_CG_PQ: dot partner (normally == x)
+    double* dot_out;     // EPI_CG_PQ: result scalar (device)
+    // grid-reduction scratch (EPI_CG_PQ)
+    double* red_partial;
+    unsigned* red_counter;
+    const int* skip_flag; // if non-null and *skip_flag != 0 the kernel returns at once
+};
+
+int launch_spmv(gse_matrix* h, int k, int epi, const SpmvArgs& a, cudaStream_t s, int upl_override = 0);
+int spmv_grid(gse_matrix* h, int upl);
+
+}  // namespace gse

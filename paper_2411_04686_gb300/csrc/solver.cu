@@ -1,0 +1,898 @@
+// solver.cu -- the stepped mixed-precision CG (Alg. 3 with the policy of
+// Sec. III-D) as a device-resident, multi-system engine.
+//
+// Every system carries a small state machine in device memory; one iteration
+// "slot" is three kernels that each process all active systems:
+//   P1  SpMV phase   ITER:    q = A_k p and p.q          (fused epilogue)
+//                    RESID_R: r = b - A_k x              (restart at level k)
+//                    RESID_T: q = b - A_kmax x           (true-residual check)
+//   P2  vector 1     ITER:    alpha = rho / p.q, r -= alpha q, rho' = r.r,
+//                             then (last block) the residual history, Eqs. 3-6,
+//                             Conditions 1-3, the convergence check and the
+//                             next mode
+//                    RESID_R: rho = r.r      RESID_T: ||q||, decide
+//   P3  vector 2     x += alpha p (the x update is folded here, one pass) and
+//                    p = r + beta p, or p = r / r = p = q after a restart
+// The host only enqueues slots and reads the state array once per batch, so a
+// single solve runs without a host round trip per iteration, and a batch of
+// systems shares each launch.  Each system's blocks, chunks and reduction
+// order depend on its own size only, so a system gives bit-identical results
+// alone and inside any batch.
+#include <chrono>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "spmv_core.cuh"
+
+namespace gse {
+
+enum { MODE_ITER = 0, MODE_RESID_R = 1, MODE_RESID_T = 2, MODE_DONE = 3 };
+enum { PA_NONE = 0, PA_UPDATE = 1, PA_XONLY = 2, PA_COPY_R = 3, PA_COPY_Q = 4, PA_ZERO_X = 5 };
+constexpr int RING_MAX = 4096;
+constexpr int ENG_WARPS = 8;
+
+struct CgState {
+    int mode, k, status, j, p_action, hlen, hpos, pad;
+    int sw[4];
+    double rho, pq, alpha, beta, nb, res, true_res, xnorm2;
+};
+
+struct CgParams {
+    int l, t, m, ndec_limit, max_iter, flags, kstart, kmax;
+    double rsd_limit, reldec_limit, tol;
+    double eta[4];
+};
+
+struct SysDesc {
+    MatView m;
+    int upl, nblk_spmv, nblk_vec, pad;
+    int64_t n, n_chunks;
+    const double* b;
+    double* x;
+    double* r;
+    double* p;
+    double* q;
+    double* ring;
+    CgState* st;
+    double* partial;
+    unsigned* counter;
+    CgParams prm;
+};
+
+struct Workspace {
+    double* r = nullptr;
+    double* p = nullptr;
+    double* q = nullptr;
+    double* ring = nullptr;
+    double* partial = nullptr;
+    unsigned* counter = nullptr;
+    int64_t n = 0;
+    int partial_cap = 0;
+    // GMRES
+    double* V = nullptr;
+    int V_cols = 0;
+    double* gm_scratch = nullptr;
+    size_t gm_scratch_n = 0;
+    bool eta_ready = false;
+    double eta[4] = {0, 0, 0, 0};
+};
+
+// ---- helpers --------------------------------------------------------------
+
+// Sum over a system's blocks: the last block (per-system counter) gets the total
+// (in every thread) and returns true.
+__device__ __forceinline__ bool sys_grid_sum(double v, double* partial, unsigned* counter, int lb,
+                                             int nblk, double* red, double* total) {
+    __shared__ bool last;
+    __shared__ double tot;
+    const double s = block_sum(v, red);
+    if (threadIdx.x == 0) {
+        partial[lb] = s;
+        __threadfence();
+        last = atomicAdd(counter, 1u) == (unsigned)nblk - 1;
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    double a = 0.0;
+    for (int i = threadIdx.x; i < nblk; i += blockDim.x) a += __ldcg(partial + i);
+    a = block_sum(a, red);
+    if (threadIdx.x == 0) {
+        tot = a;
+        *counter = 0;
+    }
+    __syncthreads();
+    *total = tot;
+    return true;
+}
+
+template <int UPL>
+__device__ __forceinline__ double run_chunk(int k, const MatView& m, const double* x, const Epi& e,
+                                            int64_t c, double* yb) {
+    switch (k) {
+        case 1: return process_chunk<1, 0, UPL>(m, x, e, c, yb);
+        case 2: return process_chunk<2, 0, UPL>(m, x, e, c, yb);
+        case 3: return process_chunk<3, -1, UPL>(m, x, e, c, yb);
+        case SRC_FP32: return process_chunk<SRC_FP32, 0, UPL>(m, x, e, c, yb);
+        default: return process_chunk<SRC_FP64, 0, UPL>(m, x, e, c, yb);
+    }
+}
+
+// ---- P1: SpMV phase -------------------------------------------------------
+
+__global__ void __launch_bounds__(256) k_cg_p1(const SysDesc* __restrict__ sys, const int2* __restrict__ map) {
+    extern __shared__ double smem[];
+    const int2 bm = map[blockIdx.x];
+    const SysDesc& S = sys[bm.x];
+    CgState* st = S.st;
+    const int mode = st->mode;
+    if (mode == MODE_DONE) return;
+    const int lb = bm.y, nblk = S.nblk_spmv;
+    const MatView m = S.m;
+    Epi e;
+    const double* x;
+    int k;
+    if (mode == MODE_ITER) {
+        e.kind = EPI_CG_PQ; e.y = S.q; e.b = nullptr; e.p = S.p; x = S.p; k = st->k;
+    } else if (mode == MODE_RESID_R) {
+        e.kind = EPI_RESID; e.y = S.r; e.b = S.b; e.p = nullptr; x = S.x; k = st->k;
+    } else {
+        e.kind = EPI_RESID; e.y = S.q; e.b = S.b; e.p = nullptr; x = S.x; k = S.prm.kmax;
+    }
+    fill_empty_rows(m, e, (int64_t)lb * blockDim.x + threadIdx.x, (int64_t)nblk * blockDim.x);
+    const int warp = threadIdx.x >> 5;
+    const int upl = S.upl;
+    double* yb = smem + warp * 512;
+    double* red = smem + ENG_WARPS * 512;
+    double dot = 0.0;
+    const int64_t nch = S.n_chunks;
+    if (upl == 1) {
+        for (int64_t c = (int64_t)lb * ENG_WARPS + warp; c < nch; c += (int64_t)nblk * ENG_WARPS)
+            dot += run_chunk<1>(k, m, x, e, c, yb);
+    } else {
+        for (int64_t c = (int64_t)lb * ENG_WARPS + warp; c < nch; c += (int64_t)nblk * ENG_WARPS)
+            dot += run_chunk<2>(k, m, x, e, c, yb);
+    }
+    if (mode == MODE_ITER) {
+        double total;
+        if (sys_grid_sum(dot, S.partial, S.counter, lb, nblk, red, &total) && threadIdx.x == 0) st->pq = total;
+    }
+}
+
+// ---- P2: residual update, history, policy, next mode ----------------------
+
+// Metrics of Eqs. 3-6 over the ring (oldest .. newest = t + 1 entries), with the
+// block's threads; results valid in thread 0.
+__device__ void ring_metrics(const double* ring, int t, int hpos, double* red, double* rsd, int* ndec,
+                             double* reldec) {
+    const int cap = t + 1;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < t; i += blockDim.x) s += ring[(hpos + i) % cap];
+    s = block_sum(s, red);
+    __shared__ double avg_sh;
+    if (threadIdx.x == 0) avg_sh = s / t;
+    __syncthreads();
+    const double avg = avg_sh;
+    double v = 0.0, nd = 0.0;
+    for (int i = threadIdx.x; i < t; i += blockDim.x) {
+        const double a = ring[(hpos + i) % cap], b = ring[(hpos + i + 1) % cap];
+        v += (a - avg) * (a - avg);
+        nd += a > b ? 1.0 : 0.0;
+    }
+    v = block_sum(v, red);
+    nd = block_sum(nd, red);
+    if (threadIdx.x == 0) {
+        *rsd = sqrt(v / t) / avg;
+        *ndec = (int)nd;
+        const double first = ring[hpos % cap], prev = ring[(hpos + t - 1) % cap];
+        *reldec = (first - prev) / first;
+    }
+}
+
+__device__ __forceinline__ bool conditions(const CgParams& P, double rsd, int ndec, double reldec) {
+    const double thr = P.ndec_limit > 0 ? (double)P.ndec_limit : 0.5 * P.t;
+    const bool c1 = rsd > P.rsd_limit && (double)ndec < thr;
+    const bool c2 = (double)ndec >= thr && reldec < P.reldec_limit;
+    const bool c3 = ndec == 0;
+    return c1 || c2 || c3;
+}
+
+__device__ __forceinline__ void step_level(CgState* st) {
+    st->k = st->k + 1;
+    st->sw[st->k - 1] = st->j;
+}
+
+__global__ void __launch_bounds__(256) k_cg_p2(const SysDesc* __restrict__ sys, const int2* __restrict__ map) {
+    __shared__ double red[32];
+    __shared__ int need_metrics;
+    __shared__ double m_rsd, m_reldec;
+    __shared__ int m_ndec;
+    const int2 bm = map[blockIdx.x];
+    const SysDesc& S = sys[bm.x];
+    CgState* st = S.st;
+    const int mode = st->mode;
+    if (mode == MODE_DONE) return;
+    const int lb = bm.y, nblk = S.nblk_vec;
+    const int64_t n = S.n;
+    double acc = 0.0, alpha = 0.0;
+    bool brk = false;
+    if (mode == MODE_ITER) {
+        const double pq = st->pq;
+        alpha = st->rho / pq;
+        brk = !(pq > 0.0) || !isfinite(pq) || !isfinite(alpha);
+        if (!brk) {
+            double* __restrict__ r = S.r;
+            const double* __restrict__ q = S.q;
+            for (int64_t i = (int64_t)lb * blockDim.x + threadIdx.x; i < n; i += (int64_t)nblk * blockDim.x) {
+                const double ri = fma(-alpha, q[i], r[i]);
+                r[i] = ri;
+                acc = fma(ri, ri, acc);
+            }
+        }
+    } else {
+        const double* __restrict__ v = mode == MODE_RESID_R ? S.r : S.q;
+        for (int64_t i = (int64_t)lb * blockDim.x + threadIdx.x; i < n; i += (int64_t)nblk * blockDim.x)
+            acc = fma(v[i], v[i], acc);
+    }
+    double total;
+    if (!sys_grid_sum(acc, S.partial, S.counter + 1, lb, nblk, red, &total)) return;
+    // ---- last block of this system: the decisions ----
+    const CgParams& P = S.prm;
+    if (threadIdx.x == 0) {
+        need_metrics = 0;
+        if (mode == MODE_ITER) {
+            st->alpha = alpha;
+            if (brk) {
+                const double pq = st->pq;
+                if (!isfinite(pq) || !isfinite(alpha)) {
+                    st->mode = MODE_DONE; st->status = GSE_NONFINITE; st->p_action = PA_NONE;
+                } else if (st->k < P.kmax) {
+                    step_level(st); st->mode = MODE_RESID_R; st->p_action = PA_NONE;
+                } else {
+                    st->mode = MODE_DONE; st->status = GSE_BREAKDOWN; st->p_action = PA_NONE;
+                }
+            } else {
+                const double res = sqrt(total) / st->nb;
+                st->j = st->j + 1;
+                st->res = res;
+                const int cap = P.t + 1;
+                S.ring[st->hpos] = res;
+                st->hpos = (st->hpos + 1) % cap;
+                if (st->hlen < cap) st->hlen = st->hlen + 1;
+                st->p_action = PA_XONLY;
+                if (!isfinite(res)) {
+                    st->mode = MODE_DONE; st->status = GSE_NONFINITE; st->p_action = PA_NONE;
+                } else if (res < P.tol) {
+                    st->mode = MODE_RESID_T;
+                } else {
+                    bool step = false;
+                    if (st->k < P.kmax && (P.flags & GSE_POLICY_FLOOR) && st->xnorm2 > 0.0) {
+                        const double floor_k = P.eta[st->k] * sqrt(st->xnorm2) / st->nb;
+                        if (res <= floor_k) step = true;
+                    }
+                    if (!step && st->k < P.kmax && !(P.flags & GSE_POLICY_NO_STAGNATION) && P.m > 0 &&
+                        st->j >= P.l && st->j % P.m == 0 && st->hlen >= cap)
+                        need_metrics = 1;
+                    if (step) {
+                        step_level(st); st->mode = MODE_RESID_R;
+                    } else if (!need_metrics) {
+                        if (st->j >= P.max_iter) {
+                            st->mode = MODE_DONE; st->status = GSE_MAXITER;
+                        } else {
+                            st->beta = total / st->rho; st->rho = total; st->p_action = PA_UPDATE;
+                        }
+                    }
+                }
+                st->pq = total;   // keep rho' until the metrics decide
+            }
+        } else if (mode == MODE_RESID_R) {
+            st->rho = total;
+            st->res = sqrt(total) / st->nb;
+            st->hlen = 0; st->hpos = 0;
+            if (st->res < P.tol) {
+                if (st->k >= P.kmax) { st->mode = MODE_DONE; st->status = GSE_OK; st->true_res = st->res; st->p_action = PA_NONE; }
+                else { st->mode = MODE_RESID_T; st->p_action = PA_NONE; }
+            } else {
+                st->mode = MODE_ITER; st->p_action = PA_COPY_R;
+            }
+        } else {  // MODE_RESID_T
+            const double tr = sqrt(total) / st->nb;
+            st->true_res = tr;
+            if (tr < P.tol) {
+                st->mode = MODE_DONE; st->status = GSE_OK; st->p_action = PA_NONE;
+            } else {
+                if (st->k < P.kmax) step_level(st);
+                if (st->k >= P.kmax) {
+                    st->rho = total; st->res = tr; st->hlen = 0; st->hpos = 0;
+                    st->mode = MODE_ITER; st->p_action = PA_COPY_Q;
+                } else {
+                    st->mode = MODE_RESID_R; st->p_action = PA_NONE;
+                }
+                if (st->j >= P.max_iter) { st->mode = MODE_DONE; st->status = GSE_MAXITER; st->p_action = PA_NONE; }
+            }
+        }
+    }
+    __syncthreads();
+    if (need_metrics) {
+        ring_metrics(S.ring, P.t, st->hpos, red, &m_rsd, &m_ndec, &m_reldec);
+        if (threadIdx.x == 0) {
+            const double rho_new = st->pq;
+            if (conditions(P, m_rsd, m_ndec, m_reldec)) {
+                step_level(st); st->mode = MODE_RESID_R;
+            } else if (st->j >= P.max_iter) {
+                st->mode = MODE_DONE; st->status = GSE_MAXITER;
+            } else {
+                st->beta = rho_new / st->rho; st->rho = rho_new; st->p_action = PA_UPDATE;
+            }
+        }
+    }
+}
+
+// ---- P3: x and p updates --------------------------------------------------
+
+__global__ void __launch_bounds__(256) k_cg_p3(const SysDesc* __restrict__ sys, const int2* __restrict__ map) {
+    __shared__ double red[32];
+    const int2 bm = map[blockIdx.x];
+    const SysDesc& S = sys[bm.x];
+    CgState* st = S.st;
+    const int pa = st->p_action;
+    if (pa == PA_NONE) return;
+    const int lb = bm.y, nblk = S.nblk_vec;
+    const int64_t n = S.n;
+    const double alpha = st->alpha, beta = st->beta;
+    double* __restrict__ x = S.x;
+    double* __restrict__ p = S.p;
+    double* __restrict__ r = S.r;
+    const double* __restrict__ q = S.q;
+    double acc = 0.0;
+    const int64_t i0 = (int64_t)lb * blockDim.x + threadIdx.x, di = (int64_t)nblk * blockDim.x;
+    if (pa == PA_UPDATE) {
+        for (int64_t i = i0; i < n; i += di) {
+            const double pi = p[i];
+            const double xi = fma(alpha, pi, x[i]);
+            x[i] = xi;
+            p[i] = fma(beta, pi, r[i]);
+            acc = fma(xi, xi, acc);
+        }
+    } else if (pa == PA_XONLY) {
+        for (int64_t i = i0; i < n; i += di) {
+            const double xi = fma(alpha, p[i], x[i]);
+            x[i] = xi;
+            acc = fma(xi, xi, acc);
+        }
+    } else if (pa == PA_COPY_R) {
+        for (int64_t i = i0; i < n; i += di) p[i] = r[i];
+    } else if (pa == PA_COPY_Q) {
+        for (int64_t i = i0; i < n; i += di) {
+            const double v = q[i];
+            r[i] = v;
+            p[i] = v;
+        }
+    } else {
+        for (int64_t i = i0; i < n; i += di) x[i] = 0.0;
+    }
+    double total;
+    if (!sys_grid_sum(acc, S.partial, S.counter + 2, lb, nblk, red, &total)) return;
+    if (threadIdx.x == 0) {
+        if (pa == PA_UPDATE || pa == PA_XONLY) st->xnorm2 = total;
+        st->p_action = PA_NONE;
+    }
+}
+
+// ---- P0: ||b|| and the initial state --------------------------------------
+
+__global__ void __launch_bounds__(256) k_cg_init(const SysDesc* __restrict__ sys, const int2* __restrict__ map) {
+    __shared__ double red[32];
+    const int2 bm = map[blockIdx.x];
+    const SysDesc& S = sys[bm.x];
+    CgState* st = S.st;
+    if (st->mode != MODE_RESID_R || st->j != -1) return;   // only freshly submitted systems
+    const int lb = bm.y, nblk = S.nblk_vec;
+    double acc = 0.0;
+    for (int64_t i = (int64_t)lb * blockDim.x + threadIdx.x; i < S.n; i += (int64_t)nblk * blockDim.x)
+        acc = fma(S.b[i], S.b[i], acc);
+    double total;
+    if (!sys_grid_sum(acc, S.partial, S.counter + 1, lb, nblk, red, &total)) return;
+    if (threadIdx.x == 0) {
+        st->nb = sqrt(total);
+        st->j = 0;
+        if (!(total > 0.0)) {
+            st->mode = MODE_DONE; st->status = isfinite(total) ? GSE_OK : GSE_NONFINITE;
+            st->res = 0.0; st->true_res = 0.0; st->p_action = PA_ZERO_X;
+        } else if (!isfinite(total)) {
+            st->mode = MODE_DONE; st->status = GSE_NONFINITE; st->p_action = PA_NONE;
+        }
+    }
+}
+
+// ---- floor coefficients (GSE_POLICY_FLOOR) --------------------------------
+// eta_k = max_i sum_j |a3_ij - ak_ij|: the infinity norm of the truncation
+// A_kmax - A_k, so that ||(A_kmax - A_k) x|| <~ eta_k ||x||.
+__global__ void k_row_absdiff_max(const int32_t* row_ptr, int64_t n, const double* a, const double* b,
+                                  unsigned long long* out) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int32_t e = row_ptr[r]; e < row_ptr[r + 1]; e++) s += fabs(a[e] - b[e]);
+        atomicMax(out, (unsigned long long)__double_as_longlong(s));
+    }
+}
+
+}  // namespace gse
+
+using namespace gse;
+
+// ---- workspace --------------------------------------------------------------
+
+void gse_free_workspace(gse_matrix* h) {
+    if (!h->ws) return;
+    Workspace* w = h->ws;
+    void* bufs[] = {w->r, w->p, w->q, w->ring, w->partial, w->counter, w->V, w->gm_scratch};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    delete w;
+    h->ws = nullptr;
+    h->bytes_ws = 0;
+}
+
+static int ensure_cg_workspace(gse_matrix* h, cudaStream_t s) {
+    if (!h->ws) h->ws = new Workspace();
+    Workspace* w = h->ws;
+    const int64_t n = h->v.n_rows;
+    if (!w->r) {
+        const size_t bytes = (size_t)(n + 1) * sizeof(double);
+        if (cudaMalloc(&w->r, bytes) != cudaSuccess || cudaMalloc(&w->p, bytes) != cudaSuccess ||
+            cudaMalloc(&w->q, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return GSE_ERR_OOM;
+        }
+        h->bytes_ws += 3 * bytes;
+        w->n = n;
+    }
+    if (!w->ring) {
+        if (cudaMalloc(&w->ring, (RING_MAX + 1) * sizeof(double)) != cudaSuccess) return GSE_ERR_OOM;
+        h->bytes_ws += (RING_MAX + 1) * sizeof(double);
+    }
+    if (!w->partial) {
+        w->partial_cap = h->num_sms * 64;
+        if (cudaMalloc(&w->partial, (size_t)w->partial_cap * sizeof(double)) != cudaSuccess ||
+            cudaMalloc(&w->counter, 8 * sizeof(unsigned)) != cudaSuccess)
+            return GSE_ERR_OOM;
+        cudaMemsetAsync(w->counter, 0, 8 * sizeof(unsigned), s);
+        h->bytes_ws += (size_t)w->partial_cap * sizeof(double) + 8 * sizeof(unsigned);
+    }
+    return GSE_OK;
+}
+
+extern "C" size_t gse_solve_footprint(gse_handle h, int method, int restart) {
+    if (!h) return 0;
+    const size_t n = (size_t)h->v.n_rows + 1;
+    size_t ws = 3 * n * sizeof(double) + (RING_MAX + 1) * sizeof(double) + (size_t)h->num_sms * 64 * sizeof(double);
+    if (method == 1) ws += (size_t)(restart + 2) * n * sizeof(double);
+    return h->bytes_matrix + ws;
+}
+
+static int compute_eta(gse_matrix* h, int kmax, cudaStream_t s) {
+    Workspace* w = h->ws;
+    if (w->eta_ready) return GSE_OK;
+    if (kmax < 1 || kmax > h->n_seg) return GSE_OK;
+    const int64_t nnz = h->v.nnz;
+    double *a = nullptr, *b = nullptr;
+    unsigned long long* d = nullptr;
+    if (cudaMalloc(&a, (nnz + 1) * sizeof(double)) != cudaSuccess || cudaMalloc(&b, (nnz + 1) * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&d, 4 * sizeof(unsigned long long)) != cudaSuccess) {
+        cudaGetLastError();
+        if (a) cudaFree(a);
+        if (b) cudaFree(b);
+        return GSE_ERR_OOM;
+    }
+    gse_decode(h, kmax, b, s);
+    for (int k = 1; k < kmax; k++) {
+        gse_decode(h, k, a, s);
+        cudaMemsetAsync(d, 0, sizeof(unsigned long long), s);
+        k_row_absdiff_max<<<1024, 256, 0, s>>>(h->v.row_ptr, h->v.n_rows, b, a, d);
+        unsigned long long bits = 0;
+        cudaMemcpyAsync(&bits, d, sizeof(bits), cudaMemcpyDeviceToHost, s);
+        cudaStreamSynchronize(s);
+        double e;
+        memcpy(&e, &bits, sizeof(e));
+        w->eta[k] = e;
+    }
+    cudaFree(a);
+    cudaFree(b);
+    cudaFree(d);
+    w->eta_ready = true;
+    return cudaGetLastError() == cudaSuccess ? GSE_OK : GSE_ERR_CUDA;
+}
+
+// ---- the engine (host side) --------------------------------------------------
+
+struct EngineSlot {
+    bool active = false;
+    bool done_reported = true;
+    gse_matrix* h = nullptr;
+    std::chrono::steady_clock::time_point t0;
+    int status_final = 0;
+};
+
+struct gse_cg_engine {
+    int capacity = 0;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int num_sms = 1;
+    int p1_resident = 1;
+    SysDesc* d_sys = nullptr;
+    CgState* d_state = nullptr;
+    CgState* h_state = nullptr;    // pinned mirror (latest completed batch)
+    CgState* h_stage[2] = {nullptr, nullptr};  // pinned landing buffers, one per batch in flight
+    int2* d_map_spmv = nullptr;
+    int2* d_map_vec = nullptr;
+    int map_cap_spmv = 0, map_cap_vec = 0;
+    int nblk_spmv = 0, nblk_vec = 0;
+    std::vector<EngineSlot> slots;
+    std::vector<SysDesc> h_sys;
+    bool dirty = true;
+    bool fresh = false;
+    cudaEvent_t ev[2];
+};
+
+static size_t p1_smem() { return (size_t)ENG_WARPS * 512 * sizeof(double) + 64 * sizeof(double); }
+
+extern "C" int gse_engine_create(int capacity, void* stream, gse_engine* out) {
+    if (capacity < 1 || !out) return GSE_ERR_INVALID;
+    gse_cg_engine* e = new gse_cg_engine();
+    e->capacity = capacity;
+    e->stream = (cudaStream_t)stream;
+    cudaGetDevice(&e->device);
+    cudaDeviceGetAttribute(&e->num_sms, cudaDevAttrMultiProcessorCount, e->device);
+    cudaFuncSetAttribute((const void*)k_cg_p1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p1_smem());
+    int nb = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cg_p1, 256, p1_smem()) != cudaSuccess || nb < 1) nb = 1;
+    e->p1_resident = nb;
+    e->slots.resize(capacity);
+    e->h_sys.resize(capacity);
+    if (cudaMalloc(&e->d_sys, capacity * sizeof(SysDesc)) != cudaSuccess ||
+        cudaMalloc(&e->d_state, capacity * sizeof(CgState)) != cudaSuccess ||
+        cudaMallocHost(&e->h_state, capacity * sizeof(CgState)) != cudaSuccess ||
+        cudaMallocHost(&e->h_stage[0], capacity * sizeof(CgState)) != cudaSuccess ||
+        cudaMallocHost(&e->h_stage[1], capacity * sizeof(CgState)) != cudaSuccess) {
+        cudaGetLastError();
+        gse_engine_destroy(e);
+        return GSE_ERR_OOM;
+    }
+    memset(e->h_state, 0, capacity * sizeof(CgState));
+    cudaEventCreateWithFlags(&e->ev[0], cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&e->ev[1], cudaEventDisableTiming);
+    *out = e;
+    return GSE_OK;
+}
+
+extern "C" void gse_engine_destroy(gse_engine e) {
+    if (!e) return;
+    if (e->stream || true) cudaStreamSynchronize(e->stream);
+    if (e->d_sys) cudaFree(e->d_sys);
+    if (e->d_state) cudaFree(e->d_state);
+    if (e->h_state) cudaFreeHost(e->h_state);
+    if (e->h_stage[0]) cudaFreeHost(e->h_stage[0]);
+    if (e->h_stage[1]) cudaFreeHost(e->h_stage[1]);
+    if (e->d_map_spmv) cudaFree(e->d_map_spmv);
+    if (e->d_map_vec) cudaFree(e->d_map_vec);
+    if (e->ev[0]) cudaEventDestroy(e->ev[0]);
+    if (e->ev[1]) cudaEventDestroy(e->ev[1]);
+    delete e;
+}
+
+static bool level_valid(const gse_matrix* h, int k) {
+    if (k >= 1 && k <= h->n_seg) return true;
+    if (k == GSE_LEVEL_FP64) return h->v.val64 != nullptr;
+    if (k == GSE_LEVEL_FP32) return h->v.val32 != nullptr;
+    return false;
+}
+
+extern "C" int gse_engine_submit(gse_engine e, gse_handle h, const double* b, double* x, double tol,
+                                 const gse_step_policy* pol, int* slot_out) {
+    if (!e || !h || !b || !x || !pol || !(tol > 0)) return GSE_ERR_INVALID;
+    if (!level_valid(h, pol->k_start) || !level_valid(h, pol->k_max)) return GSE_ERR_INVALID;
+    const bool base = pol->k_start > 3 || pol->k_max > 3;
+    if (base && pol->k_start != pol->k_max) return GSE_ERR_INVALID;
+    if (!base && pol->k_start > pol->k_max) return GSE_ERR_INVALID;
+    if (pol->t < 1 || pol->t > RING_MAX - 1 || pol->max_iter < 1) return GSE_ERR_INVALID;
+    int slot = -1;
+    for (int i = 0; i < e->capacity; i++)
+        if (e->slots[i].active && e->slots[i].h == h) return GSE_ERR_INVALID;  // one workspace per handle
+    for (int i = 0; i < e->capacity; i++)
+        if (!e->slots[i].active && e->slots[i].done_reported) { slot = i; break; }
+    if (slot < 0) return GSE_ERR_INVALID;
+    int rc = ensure_cg_workspace(h, e->stream);
+    if (rc != GSE_OK) return rc;
+    if ((pol->flags & GSE_POLICY_FLOOR) && !base) {
+        rc = compute_eta(h, pol->k_max, e->stream);
+        if (rc != GSE_OK) return rc;
+    }
+    Workspace* w = h->ws;
+    SysDesc d;
+    memset(&d, 0, sizeof(d));
+    d.m = h->v;
+    d.upl = units_per_lane(h) >= 2 ? 2 : 1;
+    d.n = h->v.n_rows;
+    d.n_chunks = (h->v.nnz + 256 * d.upl - 1) / (256 * d.upl);
+    int64_t nbs = (d.n_chunks + ENG_WARPS - 1) / ENG_WARPS;
+    const int64_t cap_s = (int64_t)e->num_sms * e->p1_resident;
+    if (nbs > cap_s) nbs = cap_s;
+    if (nbs < 1) nbs = 1;
+    int64_t nbv = (d.n + 1023) / 1024;
+    if (nbv > (int64_t)e->num_sms * 8) nbv = (int64_t)e->num_sms * 8;
+    if (nbv < 1) nbv = 1;
+    if (nbs > w->partial_cap) nbs = w->partial_cap;
+    if (nbv > w->partial_cap) nbv = w->partial_cap;
+    d.nblk_spmv = (int)nbs;
+    d.nblk_vec = (int)nbv;
+    d.b = b;
+    d.x = x;
+    d.r = w->r;
+    d.p = w->p;
+    d.q = w->q;
+    d.ring = w->ring;
+    d.st = e->d_state + slot;
+    d.partial = w->partial;
+    d.counter = w->counter;
+    d.prm.l = pol->l;
+    d.prm.t = pol->t;
+    d.prm.m = pol->m;
+    d.prm.ndec_limit = pol->ndec_limit;
+    d.prm.max_iter = pol->max_iter;
+    d.prm.flags = pol->flags;
+    d.prm.kstart = pol->k_start;
+    d.prm.kmax = pol->k_max;
+    d.prm.rsd_limit = pol->rsd_limit;
+    d.prm.reldec_limit = pol->reldec_limit;
+    d.prm.tol = tol;
+    for (int i = 0; i < 4; i++) d.prm.eta[i] = w->eta[i];
+    e->h_sys[slot] = d;
+    CgState s0;
+    memset(&s0, 0, sizeof(s0));
+    s0.mode = MODE_RESID_R;
+    s0.k = pol->k_start;
+    s0.j = -1;  // marks "needs init"
+    s0.status = GSE_MAXITER;
+    for (int i = 0; i < 4; i++) s0.sw[i] = -1;
+    if (!base) s0.sw[pol->k_start - 1] = 0;
+    e->h_state[slot] = s0;
+    cudaMemcpyAsync(e->d_sys + slot, &e->h_sys[slot], sizeof(SysDesc), cudaMemcpyHostToDevice, e->stream);
+    cudaMemcpyAsync(e->d_state + slot, &e->h_state[slot], sizeof(CgState), cudaMemcpyHostToDevice, e->stream);
+    cudaStreamSynchronize(e->stream);   // pageable/pinned sources stay valid; cheap and rare
+    e->slots[slot].active = true;
+    e->slots[slot].done_reported = false;
+    e->slots[slot].h = h;
+    e->slots[slot].t0 = std::chrono::steady_clock::now();
+    e->dirty = true;
+    e->fresh = true;
+    if (slot_out) *slot_out = slot;
+    return cudaGetLastError() == cudaSuccess ? GSE_OK : GSE_ERR_CUDA;
+}
+
+static int rebuild_maps(gse_cg_engine* e) {
+    std::vector<int2> ms, mv;
+    for (int i = 0; i < e->capacity; i++) {
+        if (!e->slots[i].active) continue;
+        const SysDesc& d = e->h_sys[i];
+        for (int b = 0; b < d.nblk_spmv; b++) ms.push_back(make_int2(i, b));
+        for (int b = 0; b < d.nblk_vec; b++) mv.push_back(make_int2(i, b));
+    }
+    auto grow = [](int2** buf, int* cap, size_t need) -> int {
+        if ((size_t)*cap >= need) return GSE_OK;
+        if (*buf) cudaFree(*buf);
+        size_t c = need + need / 2 + 16;
+        if (cudaMalloc(buf, c * sizeof(int2)) != cudaSuccess) { cudaGetLastError(); *buf = nullptr; *cap = 0; return GSE_ERR_OOM; }
+        *cap = (int)c;
+        return GSE_OK;
+    };
+    cudaStreamSynchronize(e->stream);
+    int rc = grow(&e->d_map_spmv, &e->map_cap_spmv, ms.size());
+    if (rc == GSE_OK) rc = grow(&e->d_map_vec, &e->map_cap_vec, mv.size());
+    if (rc != GSE_OK) return rc;
+    if (!ms.empty()) cudaMemcpy(e->d_map_spmv, ms.data(), ms.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    if (!mv.empty()) cudaMemcpy(e->d_map_vec, mv.data(), mv.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    e->nblk_spmv = (int)ms.size();
+    e->nblk_vec = (int)mv.size();
+    e->dirty = false;
+    return GSE_OK;
+}
+
+static void enqueue_slots(gse_cg_engine* e, int nslots) {
+    for (int it = 0; it < nslots; it++) {
+        k_cg_p1<<<e->nblk_spmv, 256, p1_smem(), e->stream>>>(e->d_sys, e->d_map_spmv);
+        k_cg_p2<<<e->nblk_vec, 256, 0, e->stream>>>(e->d_sys, e->d_map_vec);
+        k_cg_p3<<<e->nblk_vec, 256, 0, e->stream>>>(e->d_sys, e->d_map_vec);
+    }
+}
+
+static bool any_running(gse_cg_engine* e) {
+    for (int i = 0; i < e->capacity; i++)
+        if (e->slots[i].active && e->h_state[i].mode != MODE_DONE) return true;
+    return false;
+}
+
+// Advances all active systems by up to max_slots iteration slots (batches of
+// `batch`, double-buffered); returns early when every active system is done.
+extern "C" int gse_engine_run(gse_engine e, int max_slots, int batch, int* n_running) {
+    if (!e || max_slots < 0) return GSE_ERR_INVALID;
+    if (batch < 1) batch = 8;
+    if (e->dirty) {
+        const int rc = rebuild_maps(e);
+        if (rc != GSE_OK) return rc;
+    }
+    if (e->nblk_vec == 0) {
+        if (n_running) *n_running = 0;
+        return GSE_OK;
+    }
+    if (e->fresh) {
+        k_cg_init<<<e->nblk_vec, 256, 0, e->stream>>>(e->d_sys, e->d_map_vec);
+        k_cg_p3<<<e->nblk_vec, 256, 0, e->stream>>>(e->d_sys, e->d_map_vec);  // zero x for b = 0
+        e->fresh = false;
+    }
+    const size_t sbytes = e->capacity * sizeof(CgState);
+    int done_slots = 0, inflight = 0, cur = 0;
+    bool running = true;
+    while (done_slots < max_slots && running) {
+        const int nb = max_slots - done_slots < batch ? max_slots - done_slots : batch;
+        enqueue_slots(e, nb);
+        done_slots += nb;
+        cudaMemcpyAsync(e->h_stage[cur], e->d_state, sbytes, cudaMemcpyDeviceToHost, e->stream);
+        cudaEventRecord(e->ev[cur], e->stream);
+        inflight++;
+        if (inflight == 2) {
+            cudaEventSynchronize(e->ev[cur ^ 1]);
+            memcpy(e->h_state, e->h_stage[cur ^ 1], sbytes);
+            inflight = 1;
+            running = any_running(e);
+        }
+        cur ^= 1;
+    }
+    cudaStreamSynchronize(e->stream);
+    if (inflight) memcpy(e->h_state, e->h_stage[cur ^ 1], sbytes);
+    running = any_running(e);
+    if (cudaGetLastError() != cudaSuccess) return GSE_ERR_CUDA;
+    if (n_running) {
+        int c = 0;
+        for (int i = 0; i < e->capacity; i++)
+            if (e->slots[i].active && e->h_state[i].mode != MODE_DONE) c++;
+        *n_running = c;
+    }
+    return GSE_OK;
+}
+
+static void fill_info(gse_cg_engine* e, int slot, gse_solve_info* info, double rel_true) {
+    const CgState& s = e->h_state[slot];
+    info->status = s.mode == MODE_DONE ? s.status : GSE_MAXITER;
+    info->iters = s.j < 0 ? 0 : s.j;
+    const int base = e->h_sys[slot].prm.kmax > 3;
+    info->k_final = base ? 0 : s.k;
+    for (int i = 0; i < 3; i++) info->switch_iter[i] = base ? -1 : s.sw[i];
+    info->rel_res_rec = s.res;
+    info->rel_res_true = rel_true;
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - e->slots[slot].t0).count();
+}
+
+// Recomputes ||b - A_kmax x|| / ||b|| for a finished system (uses its q vector).
+static double true_residual(gse_cg_engine* e, int slot) {
+    const SysDesc& d = e->h_sys[slot];
+    gse_matrix* h = e->slots[slot].h;
+    const CgState& s = e->h_state[slot];
+    if (!(s.nb > 0)) return 0.0;
+    SpmvArgs a = {};
+    a.x = d.x;
+    a.y = d.q;
+    a.b = d.b;
+    launch_spmv(h, d.prm.kmax, EPI_RESID, a, e->stream);
+    std::vector<double> qh((size_t)d.n);
+    cudaMemcpyAsync(qh.data(), d.q, d.n * sizeof(double), cudaMemcpyDeviceToHost, e->stream);
+    cudaStreamSynchronize(e->stream);
+    double ss = 0.0;
+    for (int64_t i = 0; i < d.n; i++) ss += qh[i] * qh[i];
+    return sqrt(ss) / s.nb;
+}
+
+// Reports finished systems (slots and infos, up to max_done) and frees their slots.
+extern "C" int gse_engine_poll(gse_engine e, int* done_slots, gse_solve_info* infos, int max_done, int* n_done) {
+    if (!e) return GSE_ERR_INVALID;
+    int c = 0;
+    for (int i = 0; i < e->capacity && c < max_done; i++) {
+        EngineSlot& sl = e->slots[i];
+        if (!sl.active || e->h_state[i].mode != MODE_DONE) continue;
+        gse_solve_info info;
+        memset(&info, 0, sizeof(info));
+        fill_info(e, i, &info, true_residual(e, i));
+        if (done_slots) done_slots[c] = i;
+        if (infos) infos[c] = info;
+        sl.active = false;
+        sl.done_reported = true;
+        e->dirty = true;
+        c++;
+    }
+    if (n_done) *n_done = c;
+    return GSE_OK;
+}
+
+// Cancels a slot (its system stays where it is; info reports MAXITER).
+extern "C" int gse_engine_cancel(gse_engine e, int slot, gse_solve_info* info) {
+    if (!e || slot < 0 || slot >= e->capacity || !e->slots[slot].active) return GSE_ERR_INVALID;
+    cudaStreamSynchronize(e->stream);
+    cudaMemcpy(&e->h_state[slot], e->d_state + slot, sizeof(CgState), cudaMemcpyDeviceToHost);
+    if (info) fill_info(e, slot, info, true_residual(e, slot));
+    e->slots[slot].active = false;
+    e->slots[slot].done_reported = true;
+    e->dirty = true;
+    return GSE_OK;
+}
+
+static int solve_all(gse_cg_engine* e, int nsys, gse_solve_info* infos, int max_iter_total) {
+    int running = 1;
+    // generous slot budget: every restart and check costs one slot
+    const int budget = max_iter_total + 64 * 4;
+    int used = 0;
+    while (running && used < budget) {
+        const int chunk = budget - used < 256 ? budget - used : 256;
+        const int rc = gse_engine_run(e, chunk, 16, &running);
+        if (rc != GSE_OK) return rc;
+        used += chunk;
+    }
+    std::vector<int> slots(nsys);
+    std::vector<gse_solve_info> inf(nsys);
+    int nd = 0;
+    gse_engine_poll(e, slots.data(), inf.data(), nsys, &nd);
+    int first_bad = GSE_OK;
+    for (int i = 0; i < nd; i++) {
+        if (infos) infos[slots[i]] = inf[i];
+        if (inf[i].status != GSE_OK && first_bad == GSE_OK) first_bad = inf[i].status;
+    }
+    for (int i = 0; i < nsys; i++) {
+        if (e->slots[i].active) {
+            gse_solve_info info;
+            gse_engine_cancel(e, i, &info);
+            if (infos) infos[i] = info;
+            if (first_bad == GSE_OK) first_bad = GSE_MAXITER;
+        }
+    }
+    return first_bad;
+}
+
+extern "C" int gse_cg(gse_handle h, const double* b, double* x, double tol, const gse_step_policy* policy,
+                      gse_solve_info* info, void* stream) {
+    if (!h || !b || !x || !policy) return GSE_ERR_INVALID;
+    const auto t0 = std::chrono::steady_clock::now();
+    gse_engine e = nullptr;
+    int rc = gse_engine_create(1, stream, &e);
+    if (rc != GSE_OK) return rc;
+    rc = gse_engine_submit(e, h, b, x, tol, policy, nullptr);
+    if (rc != GSE_OK) {
+        gse_engine_destroy(e);
+        return rc;
+    }
+    gse_solve_info inf;
+    memset(&inf, 0, sizeof(inf));
+    rc = solve_all(e, 1, &inf, policy->max_iter);
+    gse_engine_destroy(e);
+    inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (info) *info = inf;
+    return rc;
+}
+
+extern "C" int gse_batch_cg(int nsys, const gse_handle* hs, const double* const* b, double* const* x, double tol,
+                            const gse_step_policy* policy, gse_solve_info* infos, void* stream) {
+    if (nsys < 1 || !hs || !b || !x || !policy) return GSE_ERR_INVALID;
+    gse_engine e = nullptr;
+    int rc = gse_engine_create(nsys, stream, &e);
+    if (rc != GSE_OK) return rc;
+    for (int i = 0; i < nsys; i++) {
+        rc = gse_engine_submit(e, hs[i], b[i], x[i], tol, policy, nullptr);
+        if (rc != GSE_OK) {
+            gse_engine_destroy(e);
+            return rc;
+        }
+    }
+    rc = solve_all(e, nsys, infos, policy->max_iter);
+    gse_engine_destroy(e);
+    return rc;
+}

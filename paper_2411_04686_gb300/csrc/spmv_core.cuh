@@ -1,0 +1,337 @@
+// spmv_core.cuh -- the GSE-SpMV chunk engine (Sec. III-C, Alg. 2 and its tail
+// variants), shared by the standalone SpMV and the solver kernels.
+//
+// Schedule: nonzero-split.  A chunk is CH = 256 * UPL consecutive nonzeros,
+// processed by one warp; lane l owns UPL consecutive units of 8 nonzeros.  Each
+// lane loads its segment words, column indices and row-end bits with 128-bit
+// loads, rebuilds each value in registers with integer operations only (leading
+// one by CLZ, exponent from the group exponent, mantissa by shifts; no
+// int->double conversion and no FP64 scaling), gathers x[col] through L1/L2 and
+// accumulates with exactly one DFMA per nonzero.  Rows that end inside a lane
+// are finished there; a row that crosses lanes is stitched by a segmented warp
+// scan of the lane carries (skipped when every lane sees a row end, which holds
+// whenever rows are at most 8 long); a row that crosses chunks is combined
+// through per-chunk scratch by the last of its chunks to finish (fixed summation
+// order, so results are deterministic).  Finished rows are staged in shared
+// memory and written back coalesced, through an epilogue.
+#pragma once
+
+#include "gse_internal.cuh"
+
+namespace gse {
+
+// Value sources: K = 1, 2, 3 are GSE levels; K = 32 / 64 the plain CSR baselines.
+enum { SRC_FP32 = 32, SRC_FP64 = 64 };
+
+// ---- decode (Alg. 2 and the concatenated tails) --------------------------------
+
+// Subnormal results only: ldexp-style rounding (exact first scaling, one rounding).
+static __device__ __noinline__ double decode_tiny(uint64_t M, int Eg, int Wk, uint32_t sign) {
+    double v = (double)M * __longlong_as_double((uint64_t)(Eg - 1023 - Wk + 1023 + 200) << 52);
+    v = v * __longlong_as_double((uint64_t)(1023 - 200) << 52);
+    return sign ? -v : v;
+}
+
+// Level 1: M_1 = head magnitude (W_1 <= 15 bits).
+__device__ __forceinline__ double decode_l1(uint32_t h, int Eg, const MatView& m) {
+    const uint32_t mag = h & ((1u << m.W1) - 1u);
+    const uint32_t sign = (h >> m.W1) & 1u;
+    const int lz = __clz(mag);                       // leading one at bit 31 - lz
+    const int expo = Eg - m.W1 + 31 - lz;
+    if (mag != 0 && expo <= 0) return decode_tiny(mag, Eg, m.W1, sign);
+    const uint32_t hi = (sign << 31) | ((uint32_t)expo << 20) | ((mag << (lz - 11)) & 0xFFFFFu);
+    return __hiloint2double((int)(mag ? hi : (sign << 31)), 0);
+}
+
+// Level 2: M_2 = head magnitude << s2 | tail1 (W_2 <= 31 bits).
+__device__ __forceinline__ double decode_l2(uint32_t h, uint32_t t1, int Eg, const MatView& m) {
+    const uint32_t M = ((h & ((1u << m.W1) - 1u)) << m.s2) | t1;
+    const uint32_t sign = (h >> m.W1) & 1u;
+    const int lz = __clz(M);
+    const int expo = Eg - m.W2 + 31 - lz;
+    if (M != 0 && expo <= 0) return decode_tiny(M, Eg, m.W2, sign);
+    const uint64_t mm = (uint64_t)M << (lz + 21);    // leading one lands on bit 52
+    const uint32_t hi = (sign << 31) | ((uint32_t)expo << 20) | ((uint32_t)(mm >> 32) & 0xFFFFFu);
+    return M ? __hiloint2double((int)hi, (int)(uint32_t)mm) : __hiloint2double((int)(sign << 31), 0);
+}
+
+// Level 3: M_3 = M_2 << s3 | tail2 (W_3 <= 63 bits).
+__device__ __forceinline__ double decode_l3(uint32_t h, uint32_t t1, uint32_t t2, int Eg,
+                                            const MatView& m) {
+    const uint64_t M = ((uint64_t)((((h & ((1u << m.W1) - 1u)) << m.s2) | t1)) << m.s3) | t2;
+    const uint32_t sign = (h >> m.W1) & 1u;
+    const int lz = __clzll(M);
+    const int expo = Eg - m.W3 + 63 - lz;
+    if (M != 0 && expo <= 0) return decode_tiny(M, Eg, m.W3, sign);
+    const int sh = lz - 11;                          // 52 - position of the leading one
+    const uint64_t mm = sh >= 0 ? (M << sh) : (M >> (-sh));
+    const uint64_t bits = ((uint64_t)sign << 63) | ((uint64_t)expo << 52) | (mm & 0xFFFFFFFFFFFFFull);
+    return M ? __longlong_as_double((long long)bits) : __longlong_as_double((long long)((uint64_t)sign << 63));
+}
+
+// FP32 -> FP64 widening with integer operations (exact; no FP64 pipe use).
+__device__ __forceinline__ double widen_f32(uint32_t f) {
+    const uint32_t sign = f & 0x80000000u;
+    const uint32_t e = (f >> 23) & 0xFFu;
+    uint32_t man = f & 0x7FFFFFu;
+    if (e == 0xFFu) return __hiloint2double((int)(sign | 0x7FF00000u | (man >> 3)), (int)(man << 29));
+    if (e == 0) {
+        if (man == 0) return __hiloint2double((int)sign, 0);
+        const int lz = __clz(man) - 8;               // normalise the subnormal
+        man = (man << (lz + 1)) & 0x7FFFFFu;
+        const uint32_t ed = 1023 - 127 - lz;
+        return __hiloint2double((int)(sign | (ed << 20) | (man >> 3)), (int)(man << 29));
+    }
+    return __hiloint2double((int)(sign | ((e + 896u) << 20) | (man >> 3)), (int)(man << 29));
+}
+
+__device__ __forceinline__ uint32_t u16_of(const uint4& w, int i) {
+    const uint32_t word = (i >> 1) == 0 ? w.x : (i >> 1) == 1 ? w.y : (i >> 1) == 2 ? w.z : w.w;
+    return (i & 1) ? (word >> 16) : (word & 0xFFFFu);
+}
+
+// Loads unit u and rebuilds its 8 values.  R: bits of tail2 kept in the packed
+// low array (0, 4, 8 or 16; -1 reads the width from the view at run time).
+template <int K, int R>
+__device__ __forceinline__ void load_unit(const MatView& m, int64_t u, int* col, double* a) {
+    const int4* c4 = reinterpret_cast<const int4*>(m.col) + 2 * u;
+    const int4 ca = __ldg(c4), cb = __ldg(c4 + 1);
+    col[0] = ca.x; col[1] = ca.y; col[2] = ca.z; col[3] = ca.w;
+    col[4] = cb.x; col[5] = cb.y; col[6] = cb.z; col[7] = cb.w;
+    if constexpr (K == SRC_FP64) {
+        const double2* v2 = reinterpret_cast<const double2*>(m.val64) + 4 * u;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const double2 d = __ldcs(v2 + j);
+            a[2 * j] = d.x;
+            a[2 * j + 1] = d.y;
+        }
+    } else if constexpr (K == SRC_FP32) {
+        const uint4* f4 = reinterpret_cast<const uint4*>(m.val32) + 2 * u;
+        const uint4 fa = __ldcs(f4), fb = __ldcs(f4 + 1);
+        a[0] = widen_f32(fa.x); a[1] = widen_f32(fa.y); a[2] = widen_f32(fa.z); a[3] = widen_f32(fa.w);
+        a[4] = widen_f32(fb.x); a[5] = widen_f32(fb.y); a[6] = widen_f32(fb.z); a[7] = widen_f32(fb.w);
+    } else {
+        const int Eg = __ldg(m.gexp + ((u * GSE_UNIT) >> m.g_shift));
+        const uint4 hw = __ldcs(reinterpret_cast<const uint4*>(m.head) + u);
+        uint4 t1w = make_uint4(0, 0, 0, 0), t2w = make_uint4(0, 0, 0, 0);
+        uint32_t lo[4] = {0, 0, 0, 0};
+        if constexpr (K >= 2) t1w = __ldcs(reinterpret_cast<const uint4*>(m.tail1) + u);
+        if constexpr (K >= 3) {
+            t2w = __ldcs(reinterpret_cast<const uint4*>(m.t2hi) + u);
+            if constexpr (R == 4) lo[0] = __ldcs(m.t2lo + u);
+            if constexpr (R == 8) { const uint2 l2 = __ldcs(reinterpret_cast<const uint2*>(m.t2lo) + u); lo[0] = l2.x; lo[1] = l2.y; }
+            if constexpr (R == 16) { const uint4 l4 = __ldcs(reinterpret_cast<const uint4*>(m.t2lo) + u); lo[0] = l4.x; lo[1] = l4.y; lo[2] = l4.z; lo[3] = l4.w; }
+            if constexpr (R < 0) {
+                if (m.r_lo == 4) lo[0] = __ldcs(m.t2lo + u);
+                else if (m.r_lo == 8) { const uint2 l2 = __ldcs(reinterpret_cast<const uint2*>(m.t2lo) + u); lo[0] = l2.x; lo[1] = l2.y; }
+                else if (m.r_lo == 16) { const uint4 l4 = __ldcs(reinterpret_cast<const uint4*>(m.t2lo) + u); lo[0] = l4.x; lo[1] = l4.y; lo[2] = l4.z; lo[3] = l4.w; }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            const uint32_t h = u16_of(hw, i);
+            if constexpr (K == 1) {
+                a[i] = decode_l1(h, Eg, m);
+            } else if constexpr (K == 2) {
+                a[i] = decode_l2(h, u16_of(t1w, i), Eg, m);
+            } else {
+                uint32_t t2 = u16_of(t2w, i);
+                if constexpr (R > 0) {
+                    const int bit = i * R;
+                    t2 = (t2 << R) | ((lo[bit >> 5] >> (bit & 31)) & ((1u << R) - 1u));
+                } else if constexpr (R < 0) {
+                    if (m.r_lo > 0) {
+                        const int bit = i * m.r_lo;
+                        t2 = (t2 << m.r_lo) | ((lo[bit >> 5] >> (bit & 31)) & ((1u << m.r_lo) - 1u));
+                    }
+                }
+                a[i] = decode_l3(h, u16_of(t1w, i), t2, Eg, m);
+            }
+        }
+    }
+}
+
+// ---- epilogues ----------------------------------------------------------------
+// EPI_STORE: y[R] = v.  EPI_RESID: y[R] = b[R] - v.  EPI_CG_PQ: y[R] = v and
+// dot += p[R] * v (linear in v, so row pieces may be added separately).
+struct Epi {
+    int kind;
+    double* y;
+    const double* b;
+    const double* p;
+};
+
+__device__ __forceinline__ void epi_finish(const Epi& e, int64_t R, double v) {
+    if (e.kind == EPI_RESID) e.y[R] = e.b[R] - v;
+    else e.y[R] = v;
+}
+
+// Maps a compact (nonempty) row index to the matrix row.
+__device__ __forceinline__ int64_t actual_row(const MatView& m, int64_t rc) {
+    return m.nzrow ? (int64_t)__ldg(m.nzrow + rc) : rc;
+}
+
+// Adds `piece` of row R (a row crossing chunks) to the chunk scratch; the last
+// chunk of the row to arrive sums the pieces in chunk order and finishes it.
+// first: this chunk holds the row's first nonzero.
+template <int CH>
+__device__ __noinline__ void combine_split(const MatView& m, const Epi& e, int64_t c, int64_t R,
+                                           double piece, bool first) {
+    if (first) m.carry[c] = piece;
+    else m.part[c] = piece;
+    const int64_t s = __ldg(m.row_ptr + R), t = __ldg(m.row_ptr + R + 1);
+    const int64_t c1 = s / CH, c2 = (t - 1) / CH;
+    __threadfence();
+    const int old = atomicAdd(m.cnt + c1, 1);
+    if (old == (int)(c2 - c1)) {
+        __threadfence();
+        double sum = __ldcg(m.carry + c1);
+        for (int64_t cc = c1 + 1; cc <= c2; cc++) sum += __ldcg(m.part + cc);
+        epi_finish(e, R, sum);
+        atomicExch(m.cnt + c1, 0);
+    }
+}
+
+// Processes chunk c (CH = 256 * UPL nonzeros) with one warp.  yb: this warp's
+// shared staging buffer of CH doubles.  Returns the lane's dot contribution
+// (EPI_CG_PQ), else 0.
+template <int K, int R, int UPL>
+__device__ __forceinline__ double process_chunk(const MatView& m, const double* __restrict__ x,
+                                                const Epi& e, int64_t c, double* yb) {
+    constexpr int CH = 256 * UPL;
+    const unsigned FULL = 0xFFFFFFFFu;
+    const int lane = threadIdx.x & 31;
+    const int64_t u0 = c * (32 * UPL) + (int64_t)lane * UPL;   // first unit of the lane
+
+    // row-end bits of the lane's 8*UPL nonzeros
+    const uint32_t wbits = __ldg(m.rowend + (u0 >> 2));
+    uint32_t bits;
+    if constexpr (UPL == 4) bits = wbits;
+    else if constexpr (UPL == 2) bits = (wbits >> ((u0 & 3) * 8)) & 0xFFFFu;
+    else bits = (wbits >> ((u0 & 3) * 8)) & 0xFFu;
+    const int cnt = __popc(bits);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const int excl = incl - cnt;
+    const int total_ends = __shfl_sync(FULL, incl, 31);
+    const int64_t row0 = __ldg(m.blk_row0 + c * UPL);
+    bool starts_mid = false;
+    if (c > 0) {
+        const int64_t pe = c * CH - 1;
+        starts_mid = !((__ldg(m.rowend + (pe >> 5)) >> (pe & 31)) & 1u);
+    }
+
+    double cur = 0.0, hp = 0.0;
+    int j = 0;
+#pragma unroll
+    for (int q = 0; q < UPL; q++) {
+        int col[8];
+        double a[8];
+        load_unit<K, R>(m, u0 + q, col, a);
+        double xv[8];
+#pragma unroll
+        for (int i = 0; i < 8; i++) xv[i] = __ldg(x + col[i]);
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            cur = fma(a[i], xv[i], cur);
+            if ((bits >> (q * 8 + i)) & 1u) {
+                if (j == 0) hp = cur;
+                else yb[excl + j] = cur;
+                j++;
+                cur = 0.0;
+            }
+        }
+    }
+    const bool seen = j > 0;
+    const double co = cur;
+    double out, in;
+    if (__all_sync(FULL, seen)) {
+        out = co;
+    } else {
+        // segmented inclusive scan: out_i = co_i + (seen_i ? 0 : out_{i-1})
+        double v = co;
+        bool f = seen;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const double vu = __shfl_up_sync(FULL, v, o);
+            const bool fu = __shfl_up_sync(FULL, (int)f, o) != 0;
+            if (lane >= o) {
+                if (!f) v += vu;
+                f = f || fu;
+            }
+        }
+        out = v;
+    }
+    in = __shfl_up_sync(FULL, out, 1);
+    if (lane == 0) in = 0.0;
+    if (seen) yb[excl] = in + hp;
+    const double out31 = __shfl_sync(FULL, out, 31);
+    const bool last_end = __shfl_sync(FULL, (bits >> (8 * UPL - 1)) & 1u, 31) != 0;
+    __syncwarp();
+
+    double dot = 0.0;
+    // finished rows of this chunk, coalesced
+    for (int idx = lane; idx < total_ends; idx += 32) {
+        if (idx == 0 && starts_mid) continue;
+        const int64_t Rw = actual_row(m, row0 + idx);
+        const double v = yb[idx];
+        if (e.kind == EPI_CG_PQ) dot = fma(__ldg(e.p + Rw), v, dot);
+        epi_finish(e, Rw, v);
+    }
+    // rows crossing the chunk boundary
+    if (lane == 0) {
+        if (total_ends == 0) {
+            if (row0 < m.n_nonempty) {
+                const int64_t Rw = actual_row(m, row0);
+                if (e.kind == EPI_CG_PQ) dot = fma(__ldg(e.p + Rw), out31, dot);
+                combine_split<CH>(m, e, c, Rw, out31, !starts_mid);
+            }
+        } else {
+            if (starts_mid) {
+                const int64_t Rw = actual_row(m, row0);
+                if (e.kind == EPI_CG_PQ) dot = fma(__ldg(e.p + Rw), yb[0], dot);
+                combine_split<CH>(m, e, c, Rw, yb[0], false);
+            }
+            const int64_t ro = row0 + total_ends;
+            if (!last_end && ro < m.n_nonempty) {
+                const int64_t Rw = actual_row(m, ro);
+                if (e.kind == EPI_CG_PQ) dot = fma(__ldg(e.p + Rw), out31, dot);
+                combine_split<CH>(m, e, c, Rw, out31, true);
+            }
+        }
+    }
+    __syncwarp();
+    return dot;
+}
+
+// Zero rows (every SpMV writes them: y = 0, or y = b for the residual form).
+__device__ __forceinline__ void fill_empty_rows(const MatView& m, const Epi& e, int64_t tid,
+                                                int64_t nthreads) {
+    for (int64_t i = tid; i < m.n_empty; i += nthreads) {
+        const int64_t R = __ldg(m.empty + i);
+        epi_finish(e, R, 0.0);
+    }
+}
+
+// Deterministic sum of one double per thread of the block into red[0]
+// (thread 0 holds the result).  red: >= blockDim/32 doubles of shared memory.
+__device__ __forceinline__ double block_sum(double v, double* red) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < (int)(blockDim.x >> 5); i++) s += red[i];
+    }
+    return s;
+}
+
+}  // namespace gse

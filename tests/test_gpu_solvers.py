@@ -1,0 +1,149 @@
+"""GPU stepped CG / GMRES (Alg. 3, Sec. III-D) against the oracle: each solve
+reports its iterations and true residual and its solution is compared with the
+oracle's FP64 solve; batched and engine (served) solves equal solo solves."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2411_04686_gb300 as gse  # noqa: E402
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _solve(A, method="cg", policy=gse.SCALED_CG, tol=1e-10, attach=(64,)):
+    M = gse.GseMatrix.from_csr(A, attach=attach)
+    b = synth.rhs_ones(A)
+    x = torch.zeros(A.n_rows, dtype=torch.float64, device="cuda")
+    info = (M.cg if method == "cg" else M.gmres)(_dev(b), x, tol=tol, policy=policy)
+    return M, b, x.cpu().numpy(), info
+
+
+def test_fp64_cg_matches_oracle():
+    A = synth.poisson2d(32)
+    M, b, x, info = _solve(A, policy=gse.fp64_policy(gse.SCALED_CG))
+    ref = oracle.cg(A.row_ptr, A.col, A.val, b, tol=1e-10)
+    assert info["status"] == gse.OK
+    assert abs(info["iters"] - ref["info"]["iters"]) <= 2
+    assert info["rel_res_true"] < 1e-10
+    assert np.max(np.abs(x - ref["x"])) < 1e-8
+
+
+def test_stepped_cg_exact_head_stays_at_level1():
+    A = synth.poisson2d(32)
+    M, b, x, info = _solve(A)
+    ref = oracle.stepped_cg(A.row_ptr, A.col, oracle.levels(A.val), b, tol=1e-10, policy=oracle.SCALED_CG)
+    assert info["status"] == gse.OK and info["k_final"] == 1
+    assert info["switch_iter"][1] == -1
+    assert abs(info["iters"] - ref["info"]["iters"]) <= 2
+    assert np.max(np.abs(x - 1.0)) < 1e-7
+
+
+def test_stepped_cg_steps_on_non_dyadic_values():
+    A = synth.poisson2d(32, 1.0 / 3.0)
+    M, b, x, info = _solve(A)
+    ref = oracle.stepped_cg(A.row_ptr, A.col, oracle.levels(A.val), b, tol=1e-10, policy=oracle.SCALED_CG)
+    assert info["status"] == gse.OK and info["k_final"] == 3
+    assert info["rel_res_true"] < 1e-10
+    # same path as the oracle up to rounding: level switches within a few iterations
+    for i in (1, 2):
+        assert abs(info["switch_iter"][i] - ref["info"]["switch_iter"][i]) <= 3
+    r = b - oracle.spmv(A.row_ptr, A.col, A.val, x)
+    assert np.linalg.norm(r) / np.linalg.norm(b) < 2e-10
+    assert np.max(np.abs(x - ref["x"])) < 1e-8
+
+
+def test_floor_policy_steps_earlier_and_converges():
+    A = synth.laplace3d(16, shift=1e-3)
+    pol = gse.Policy(**{**gse.SCALED_CG.__dict__, "flags": gse.POLICY_FLOOR})
+    M, b, x, info = _solve(A, policy=pol)
+    assert info["status"] == gse.OK and info["k_final"] == 3 and info["rel_res_true"] < 1e-10
+    M2, _, x2, info2 = _solve(A)
+    assert info["switch_iter"][1] < info2["switch_iter"][1]
+    ref = oracle.cg(A.row_ptr, A.col, A.val, b, tol=1e-12)
+    assert np.max(np.abs(x - ref["x"])) < 1e-7
+
+
+def test_cg_zero_rhs_and_nonfinite():
+    A = synth.poisson2d(8)
+    M = gse.GseMatrix.from_csr(A)
+    x = torch.ones(A.n_rows, dtype=torch.float64, device="cuda")
+    info = M.cg(torch.zeros(A.n_rows, dtype=torch.float64, device="cuda"), x)
+    assert info["status"] == gse.OK and torch.all(x == 0)
+    b = torch.ones(A.n_rows, dtype=torch.float64, device="cuda")
+    b[3] = float("nan")
+    x.zero_()
+    info = M.cg(b, x)
+    assert info["status"] == gse.NONFINITE
+
+
+def test_stepped_gmres_against_oracle():
+    A = synth.convdiff2d(32, peclet=10.0).scaled(1.0 / 3.0)
+    M, b, x, info = _solve(A, method="gmres", policy=gse.SCALED_GMRES)
+    ref = oracle.stepped_gmres(A.row_ptr, A.col, oracle.levels(A.val), b, tol=1e-10,
+                               policy=oracle.SCALED_GMRES)
+    assert info["status"] == gse.OK and info["k_final"] == 3 and info["rel_res_true"] < 1e-10
+    assert abs(info["iters"] - ref["info"]["iters"]) <= 0.1 * ref["info"]["iters"] + 5
+    assert np.max(np.abs(x - ref["x"])) < 1e-7
+
+
+def test_fp64_gmres_matches_oracle():
+    A = synth.convdiff2d(40, peclet=10.0)
+    M, b, x, info = _solve(A, method="gmres", policy=gse.fp64_policy(gse.SCALED_GMRES))
+    ref = oracle.gmres(A.row_ptr, A.col, A.val, b, tol=1e-10)
+    assert info["status"] == gse.OK and info["rel_res_true"] < 1e-10
+    assert abs(info["iters"] - ref["info"]["iters"]) <= 3
+    assert np.max(np.abs(x - ref["x"])) < 1e-8
+
+
+def _systems(count, seed):
+    specs = synth.batch_specs(count, seed=seed, n_lo=200, n_hi=20000)
+    return [s.build() for s in specs]
+
+
+def test_batch_equals_solo_bitwise():
+    As = _systems(12, 5)
+    mats = [gse.GseMatrix.from_csr(A) for A in As]
+    bs = [_dev(synth.rhs_ones(A)) for A in As]
+    xs = [torch.zeros(A.n_rows, dtype=torch.float64, device="cuda") for A in As]
+    rc, infos = gse.batch_cg(mats, bs, xs)
+    assert rc == gse.OK
+    for M, A, b, xb, ib in zip(mats, As, bs, xs, infos):
+        x1 = torch.zeros(A.n_rows, dtype=torch.float64, device="cuda")
+        i1 = M.cg(b, x1)
+        assert ib["status"] == gse.OK and ib["rel_res_true"] < 1e-10
+        assert ib["iters"] == i1["iters"] and ib["switch_iter"] == i1["switch_iter"]
+        assert torch.equal(xb, x1)
+
+
+def test_engine_continuous_batching_matches_solo():
+    As = _systems(10, 6)
+    mats = [gse.GseMatrix.from_csr(A) for A in As]
+    bs = [_dev(synth.rhs_ones(A)) for A in As]
+    eng = gse.Engine(4)
+    xs = {}
+    pending = list(range(len(As)))
+    slot_of = {}
+    results = {}
+    while pending or slot_of:
+        while pending and len(slot_of) < 4:
+            i = pending.pop(0)
+            xs[i] = torch.zeros(As[i].n_rows, dtype=torch.float64, device="cuda")
+            s = eng.submit(mats[i], bs[i], xs[i])
+            slot_of[s] = i
+        eng.run(7, batch=4)      # few slots per call: systems join mid-flight
+        for s, info in eng.poll():
+            results[slot_of.pop(s)] = info
+    eng.close()
+    for i, A in enumerate(As):
+        x1 = torch.zeros(A.n_rows, dtype=torch.float64, device="cuda")
+        i1 = mats[i].cg(bs[i], x1)
+        assert results[i]["status"] == gse.OK
+        assert results[i]["iters"] == i1["iters"]
+        assert torch.equal(xs[i], x1)

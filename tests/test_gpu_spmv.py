@@ -1,0 +1,112 @@
+"""GPU GSE-SpMV (Sec. III-C, Alg. 2 and its tail variants) and the FP64/FP32 CSR
+baselines vs the oracle: every row within 1e-13 * sum_j |a_ij x_j| of the
+compensated (Dot2) oracle sum over the same decoded values; empty rows exactly 0."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import check_spmv_rows
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2411_04686_gb300 as gse  # noqa: E402
+
+
+def _with_empty_rows(seed):
+    rng = np.random.default_rng(seed)
+    n, m = 4000, 3000
+    lens = rng.integers(0, 40, n)
+    lens[:5] = 0
+    lens[-7:] = 0
+    lens[rng.random(n) < 0.2] = 0
+    rp = np.zeros(n + 1, np.int64)
+    np.cumsum(lens, out=rp[1:])
+    col = np.concatenate([np.sort(rng.choice(m, L, replace=False)) for L in lens])
+    val = rng.normal(size=rp[-1]) * 10.0 ** rng.uniform(-5, 5, rp[-1])
+    return synth.CSR(rp.astype(np.int32), col.astype(np.int32), val, m, "empty_rows")
+
+
+def _one_long_row():
+    n_cols = 20000
+    rng = np.random.default_rng(7)
+    col = np.sort(rng.choice(n_cols, 9000, replace=False))
+    rp = np.array([0, 3, 3, 3 + 9000, 3 + 9000 + 5], np.int32)
+    cols = np.concatenate([[1, 5, 9], col, [0, 1, 2, 3, 4]]).astype(np.int32)
+    val = rng.normal(size=cols.size)
+    return synth.CSR(rp, cols, val, n_cols, "long_row")
+
+
+MATS = {
+    "poisson32": lambda: synth.poisson2d(32),
+    "poisson32_third": lambda: synth.poisson2d(32, 1.0 / 3.0),
+    "laplace3d_24": lambda: synth.laplace3d(24, shift=1e-3),
+    "powerlaw_50k": lambda: synth.powerlaw_random(50000, 16.0, 2048, seed=11),
+    "empty_rows": lambda: _with_empty_rows(12),
+    "long_row": _one_long_row,
+    "tiny": lambda: synth.CSR(np.array([0, 1, 3], np.int32), np.array([1, 0, 1], np.int32),
+                              np.array([2.5, -1.0, 1 / 3]), 2, "tiny"),
+    "all_empty": lambda: synth.CSR(np.zeros(6, np.int32), np.zeros(0, np.int32), np.zeros(0), 4, "empty"),
+}
+
+
+@pytest.mark.parametrize("name", list(MATS))
+@pytest.mark.parametrize("upl", [1, 2, 4])
+def test_spmv_levels_against_oracle(name, upl):
+    A = MATS[name]()
+    M = gse.GseMatrix.from_csr(A, attach=(64, 32))
+    M.set_schedule(upl)
+    x = synth.uniform_x(A.n_cols, seed=3)
+    xd = torch.from_numpy(x).cuda()
+    enc = oracle.encode(A.val)
+    for k in (1, 2, 3):
+        ak = oracle.decode(*enc, k)
+        y = M.spmv(k, xd).cpu().numpy()
+        check_spmv_rows(y, A, ak, x)
+        # deterministic: a second run is bit-identical
+        y2 = M.spmv(k, xd).cpu().numpy()
+        assert np.array_equal(y.view(np.uint64), y2.view(np.uint64))
+    y64 = M.spmv(gse.LEVEL_FP64, xd).cpu().numpy()
+    check_spmv_rows(y64, A, A.val, x)
+    y32 = M.spmv(gse.LEVEL_FP32, xd).cpu().numpy()
+    check_spmv_rows(y32, A, A.val.astype(np.float32).astype(np.float64), x)
+    M.free()
+
+
+def test_x_ones_integer_matrix_exact():
+    """Sec. IV-A's x = 1 setting: 5-point Poisson at every level is exact."""
+    A = synth.poisson2d(64)
+    M = gse.GseMatrix.from_csr(A)
+    ones = torch.ones(A.n_cols, dtype=torch.float64, device="cuda")
+    deg = np.diff(A.row_ptr) - 1
+    for k in (1, 2, 3):
+        assert np.array_equal(M.spmv(k, ones).cpu().numpy(), 4.0 - deg)
+
+
+@pytest.mark.parametrize("which", ["laplace3d_128", "powerlaw_1m"])
+def test_full_size_sampled_rows(which):
+    """The benchmark matrices at full size, in the launch configuration the
+    benchmark times: 4000 sampled rows checked against the oracle."""
+    A = synth.laplace3d(128) if which == "laplace3d_128" else synth.powerlaw_random(1_000_000, 16.0, 2048, seed=0)
+    M = gse.GseMatrix.from_csr(A, attach=(64, 32))
+    x = synth.uniform_x(A.n_cols, seed=0)
+    xd = torch.from_numpy(x).cuda()
+    rng = np.random.default_rng(1)
+    rows = np.unique(np.concatenate([rng.choice(A.n_rows, 4000, replace=False),
+                                     [0, A.n_rows - 1, int(np.argmax(np.diff(A.row_ptr)))]]))
+    enc = oracle.encode(A.val)
+    for k in (1, 2, 3):
+        ak = oracle.decode(*enc, k)
+        check_spmv_rows(M.spmv(k, xd).cpu().numpy(), A, ak, x, rows=rows)
+    check_spmv_rows(M.spmv(gse.LEVEL_FP64, xd).cpu().numpy(), A, A.val, x, rows=rows)
+    M.free()
+
+
+def test_bad_level_rejected():
+    A = synth.poisson2d(8)
+    M = gse.GseMatrix.from_csr(A, seg_bits=(16, 16))
+    x = torch.zeros(A.n_cols, dtype=torch.float64, device="cuda")
+    for k in (0, 3, 64, 32):
+        with pytest.raises(gse.GseError):
+            M.spmv(k, x)
