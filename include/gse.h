@@ -189,6 +189,28 @@ int gse_engine_poll(gse_engine e, int* done_slots, gse_solve_info* infos, int ma
 int gse_engine_cancel(gse_engine e, int slot, gse_solve_info* info);
 void gse_engine_destroy(gse_engine e);
 
+/*
+ * gse_cg_noalloc: the stepped CG of gse_cg for callers that cannot allocate
+ * device memory once their set-up is done (a real-time loop with a fixed
+ * memory budget, code under an allocator that forbids new allocations, a
+ * thread that must not let cudaMalloc/cudaFree synchronise the device).  The
+ * paper has no counterpart; this is a deployment variant.
+ *  - Allocates nothing: no cudaMalloc, cudaFree or allocating library call.
+ *    Its Krylov vectors, history, reduction scratch, descriptor and state live
+ *    in one fixed device array inside the library (about 1.7 MB, held by every
+ *    GPU that loads the library until the process exits).
+ *  - Limit: h must have at most 65536 rows; larger systems and the
+ *    GSE_POLICY_FLOOR flag are rejected with GSE_ERR_UNSUPPORTED.
+ *  - The first call on a device looks up that array's device address (once
+ *    per device, with the device current); make that first call before any
+ *    stream capture.
+ *  - All calls share the array and each call re-initialises it; calls whose
+ *    GPU work overlaps (two threads, two streams) race and corrupt each other.
+ * Arguments, results and status codes as gse_cg; the solution equals gse_cg's.
+ */
+int gse_cg_noalloc(gse_handle h, const double* b, double* x, double tol, const gse_step_policy* policy,
+                   gse_solve_info* info, void* stream);
+
 /* Host copies of the logical segments (tests): head[nnz], tail1[nnz],
  * tail2[nnz] (the s3-bit field, widened to 32 bits), gexp[n_groups].  Any
  * pointer may be NULL to skip that array.  Synchronises the handle's stream. */

@@ -22,7 +22,7 @@ LEVEL_FP64, LEVEL_FP32 = 64, 32
 POLICY_NO_STAGNATION, POLICY_FLOOR = 1, 2
 
 # every symbol include/gse.h declares
-EXPORTS = ["gse_strerror", "gse_encode", "gse_attach_values", "gse_spmv", "gse_cg", "gse_gmres",
+EXPORTS = ["gse_strerror", "gse_encode", "gse_attach_values", "gse_spmv", "gse_cg", "gse_cg_noalloc", "gse_gmres",
            "gse_batch_cg", "gse_engine_create", "gse_engine_submit", "gse_engine_run",
            "gse_engine_poll", "gse_engine_cancel", "gse_engine_destroy", "gse_export", "gse_decode",
            "gse_matrix_get_info", "gse_set_schedule", "gse_autotune", "gse_footprint",
@@ -89,7 +89,7 @@ def lib():
     L.gse_encode.argtypes = [ctypes.POINTER(CSR), _I, _P, _I, _P, ctypes.POINTER(_P)]
     L.gse_attach_values.argtypes = [_P, ctypes.POINTER(CSR), _I, _P]
     L.gse_spmv.argtypes = [_P, _I, _P, _P, _P]
-    for f in (L.gse_cg, L.gse_gmres):
+    for f in (L.gse_cg, L.gse_cg_noalloc, L.gse_gmres):
         f.argtypes = [_P, _P, _P, _D, ctypes.POINTER(StepPolicy), ctypes.POINTER(SolveInfo), _P]
     L.gse_batch_cg.argtypes = [_I, _P, _P, _P, _D, ctypes.POINTER(StepPolicy), _P, _P]
     L.gse_engine_create.argtypes = [_I, _P, ctypes.POINTER(_P)]
