@@ -97,7 +97,7 @@ typedef struct {
     int group_size, n_seg, seg_bits[3];
     int max_row_len;
     double mean_row_len;
-    int schedule;                 /* nonzeros per lane-unit chunk: 1, 2 or 4 units */
+    int schedule;                 /* 1, 2, 4 (nonzero split) or GSE_SCHEDULE_ROWS */
     int64_t bytes_level[3];       /* algorithmic bytes read+written by one SpMV   */
 } gse_matrix_info;
 
@@ -222,9 +222,12 @@ int gse_decode(gse_handle h, int k, double* vals, void* stream);
 /* Describes the handle. */
 int gse_matrix_get_info(gse_handle h, gse_matrix_info* info);
 
-/* Force the SpMV schedule (units of 8 nonzeros per lane: 1, 2 or 4); 0 restores
- * the automatic choice. */
-int gse_set_schedule(gse_handle h, int units_per_lane);
+/* Force the SpMV schedule: 1, 2 or 4 = nonzero split, that many units of 8
+ * consecutive nonzeros per lane; GSE_SCHEDULE_ROWS = one row per lane, 32
+ * consecutive rows per warp (only for matrices whose 32-row blocks hold at most
+ * 1024 nonzeros, else GSE_ERR_UNSUPPORTED); 0 restores the automatic choice. */
+#define GSE_SCHEDULE_ROWS 8
+int gse_set_schedule(gse_handle h, int schedule);
 
 /* Time each schedule on this matrix at level k (CUDA events, a few reps) and
  * keep the fastest. */

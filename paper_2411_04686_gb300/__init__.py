@@ -20,6 +20,7 @@ OK, MAXITER, BREAKDOWN, NONFINITE, TIMEOUT = 0, 1, 2, 3, 4
 ERR_INVALID, ERR_NONFINITE, ERR_OOM, ERR_CUDA, ERR_UNSUPPORTED = -1, -2, -3, -4, -5
 LEVEL_FP64, LEVEL_FP32 = 64, 32
 POLICY_NO_STAGNATION, POLICY_FLOOR = 1, 2
+SCHEDULE_ROWS = 8
 
 # every symbol include/gse.h declares
 EXPORTS = ["gse_strerror", "gse_encode", "gse_attach_values", "gse_spmv", "gse_cg", "gse_cg_noalloc", "gse_gmres",

@@ -92,6 +92,18 @@ __global__ void k_rowend(const int32_t* row_ptr, int64_t n, uint32_t* rowend, in
     }
 }
 
+// Widest nonzero span of a block of RB consecutive rows, widened to whole
+// groups of 32 nonzeros.
+__global__ void k_row_span(const int32_t* row_ptr, int64_t n, int RB, int* out) {
+    const int64_t nb = (n + RB - 1) / RB;
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r1 = b * RB + RB < n ? b * RB + RB : n;
+        const int64_t s = row_ptr[b * RB], t = row_ptr[r1];
+        const int64_t span = (((t + 31) >> 5) << 5) - ((s >> 5) << 5);
+        atomicMax(out, (int)(span < (1 << 30) ? span : (1 << 30)));
+    }
+}
+
 __global__ void k_block_popc(const uint32_t* rowend, int64_t nblk, int* out) {
     for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nblk; b += (int64_t)gridDim.x * blockDim.x) {
         int s = 0;
@@ -225,8 +237,8 @@ static unsigned grid_for(int64_t n, int threads = 256) {
 static void free_all(gse_matrix* h) {
     void* bufs[] = {h->buf_col, h->buf_head, h->buf_tail1, h->buf_t2hi, h->buf_t2lo, h->buf_gexp,
                     h->buf_rowend, h->buf_blk_row0, h->buf_nzrow, h->buf_empty, h->buf_row_ptr,
-                    h->buf_val64, h->buf_val32, h->buf_carry, h->buf_part, h->buf_cnt,
-                    h->red_partial, h->red_counter, h->red_result};
+                    h->buf_val64, h->buf_val32, h->buf_carry, h->buf_part,
+                    h->red_partial, h->red_counter, h->red_result, h->d_err};
     for (void* b : bufs)
         if (b) cudaFree(b);
 }
@@ -305,11 +317,11 @@ static int encode_impl(const gse_csr* csr, int G, const int* seg_bits, int n_seg
     ALLOC(h->buf_blk_row0, int32_t, nblk + 1);
     ALLOC(h->buf_carry, double, nblk);
     ALLOC(h->buf_part, double, nblk);
-    ALLOC(h->buf_cnt, int32_t, nblk);
     h->red_capacity = h->num_sms * 32;
     ALLOC(h->red_partial, double, h->red_capacity);
     ALLOC(h->red_counter, unsigned, 4);
     ALLOC(h->red_result, double, 4);
+    ALLOC(h->d_err, int, 4);
     h->bytes_matrix = acc;
     // temporaries
     int *d_err = nullptr, *d_tmp = nullptr, *d_flag = nullptr, *d_flag2 = nullptr, *d_pos = nullptr;
@@ -389,11 +401,20 @@ static int encode_impl(const gse_csr* csr, int G, const int* seg_bits, int n_seg
                 }
             }
             if (status == GSE_OK) {
+                cudaMemsetAsync(d_err + 4, 0, 3 * sizeof(int), s);
+                const int rbs[3] = {32, 128, 256};
+                for (int q = 0; q < 3; q++)
+                    if (n > 0) k_row_span<<<grid_for((n + rbs[q] - 1) / rbs[q]), 256, 0, s>>>(rp, n, rbs[q], d_err + 4 + q);
+                int span[3] = {0, 0, 0};
+                cudaMemcpyAsync(span, d_err + 4, 3 * sizeof(int), cudaMemcpyDeviceToHost, s);
                 k_block_popc<<<grid_for(nblk), 256, 0, s>>>((uint32_t*)h->buf_rowend, nblk, d_flag);
                 exclusive_scan(d_flag, nblk, (int*)h->buf_blk_row0, d_scan_tmp, d_total, s);
-                cudaMemsetAsync(h->buf_cnt, 0, nblk * sizeof(int32_t), s);
                 cudaMemsetAsync(h->red_counter, 0, 4 * sizeof(unsigned), s);
+                cudaMemsetAsync(h->d_err, 0, 4 * sizeof(int), s);
                 if (cudaStreamSynchronize(s) != cudaSuccess) status = GSE_ERR_CUDA;
+                h->row_span = span[0];
+                h->row_span128 = span[1];
+                h->row_span256 = span[2];
             }
         }
     }
@@ -419,11 +440,10 @@ static int encode_impl(const gse_csr* csr, int G, const int* seg_bits, int n_seg
     v.row_ptr = (const int32_t*)h->buf_row_ptr;
     v.carry = (double*)h->buf_carry;
     v.part = (double*)h->buf_part;
-    v.cnt = (int32_t*)h->buf_cnt;
     h->mean_row_len = n > 0 ? (double)nnz / (double)n : 0.0;
-    // schedule: short rows favour 1 unit of 8 per lane (fewer idle lanes per
-    // chunk), longer rows 2 (fewer chunk overheads)
-    h->schedule_auto = h->mean_row_len <= 10.0 ? 1 : 2;
+    // schedule: short rows in every 32-row block -> one row per lane; otherwise
+    // the nonzero split, 2 units of 8 per lane (gse_autotune refines this)
+    h->schedule_auto = h->row_span256 <= GSE_ROW_SPAN_MAX && h->max_row_len <= 64 ? GSE_SCHEDULE_ROWS : 2;
     h->schedule_forced = 0;
     return GSE_OK;
 #undef ALLOC

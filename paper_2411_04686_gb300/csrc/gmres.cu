@@ -447,6 +447,12 @@ extern "C" int gse_gmres(gse_handle h, const double* b, double* x, double tol, c
     }
     cudaStreamSynchronize(s);
     gm_release(w);
+    int err = 0;
+    cudaMemcpy(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (err && status != GSE_ERR_CUDA) {
+        status = GSE_TIMEOUT;   // a bounded device-side wait gave up
+        if (info) info->status = status;
+    }
     if (status == GSE_ERR_CUDA) return status;
     return cudaGetLastError() == cudaSuccess ? status : GSE_ERR_CUDA;
 }

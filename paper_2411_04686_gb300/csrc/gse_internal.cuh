@@ -15,7 +15,8 @@
 //   nzrow   int32[n_nonempty]         compact -> actual row (only with empty rows)
 //   empty   int32[n_empty]            the empty rows (zero-filled by every SpMV)
 // Split-row scratch (rows spanning chunks), indexed by 256-nonzero block:
-//   carry f64, part f64, cnt int32 (cnt zeroed once; every SpMV leaves it zero).
+//   carry f64 (piece of the row open at a chunk's end), part f64 (piece of the
+//   row open at its start); finished by a separate pass after each SpMV.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -26,6 +27,7 @@
 #define GSE_CHUNK_BASE 256   // nonzeros per lane-unit chunk with 1 unit per lane
 #define GSE_CHUNK_MAX 1024   // with 4 units per lane
 #define GSE_UNIT 8           // consecutive nonzeros per unit
+#define GSE_ROW_SPAN_MAX 4096  // largest nonzero span of a row block the row schedule stages
 
 namespace gse {
 
@@ -46,7 +48,6 @@ struct MatView {
     const float* val32;
     double* carry;
     double* part;
-    int32_t* cnt;
     int64_t nnz, nnz_pad, n_rows, n_cols, n_nonempty, n_empty;
     int g_shift;               // log2(group size)
     int s1, s2, s3, s3hi, r_lo; // segment widths; s3hi = min(s3,16), r_lo = s3 - s3hi
@@ -64,7 +65,10 @@ struct gse_matrix {
     int seg_bits[3];
     int max_row_len;
     double mean_row_len;
-    int schedule_auto;   // units per lane chosen from row statistics / autotune
+    int schedule_auto;   // units per lane (1, 2, 4) or GSE_SCHEDULE_ROWS, from row statistics / autotune
+    int row_span;        // max nonzeros of any 32-row block, widened to groups of 32
+    int row_span128;     // ... of any 128-row block (engine: 4-warp CTAs)
+    int row_span256;     // ... of any 256-row block (standalone SpMV: 8-warp CTAs)
     int schedule_forced; // 0: automatic
     int num_sms;
     int device;
@@ -84,13 +88,13 @@ struct gse_matrix {
     void* buf_val32;
     void* buf_carry;
     void* buf_part;
-    void* buf_cnt;
     // small scratch for grid reductions
     double* red_partial;   // one per block
     unsigned* red_counter;
     double* red_result;
     int red_capacity;
     size_t bytes_matrix;
+    int* d_err;            // bounded-wait timeouts recorded by kernels (GSE_TIMEOUT)
     gse::Workspace* ws;
     size_t bytes_ws;
 };
@@ -127,6 +131,5 @@ struct SpmvArgs {
 };
 
 int launch_spmv(gse_matrix* h, int k, int epi, const SpmvArgs& a, cudaStream_t s, int upl_override = 0);
-int spmv_grid(gse_matrix* h, int upl);
 
 }  // namespace gse

@@ -118,28 +118,18 @@ extern "C" int gse_cg_noalloc(gse_handle h, const double* b, double* x, double t
     int dev = 0, num_sms = 1, resident = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute((const void*)k_cg_p1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p1_smem());
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_cg_p1, 256, p1_smem()) != cudaSuccess ||
+    cudaFuncSetAttribute((const void*)k_cg_p1, cudaFuncAttributeMaxDynamicSharedMemorySize, ENG_WARPS * eng_max_warp_smem());
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_cg_p1, ENG_WARPS * 32, p1_smem()) != cudaSuccess ||
         resident < 1)
         resident = 1;
     SysDesc d;
     memset(&d, 0, sizeof(d));
     d.m = h->v;
-    d.upl = units_per_lane(h) >= 2 ? 2 : 1;
-    d.n = h->v.n_rows;
-    d.n_chunks = (h->v.nnz + 256 * d.upl - 1) / (256 * d.upl);
-    const int64_t partial_cap = (int64_t)num_sms * 64;
-    int64_t nbs = (d.n_chunks + ENG_WARPS - 1) / ENG_WARPS;
-    if (nbs > (int64_t)num_sms * resident) nbs = (int64_t)num_sms * resident;
-    if (nbs < 1) nbs = 1;
-    int64_t nbv = (d.n + 1023) / 1024;
-    if (nbv > (int64_t)num_sms * 8) nbv = (int64_t)num_sms * 8;
-    if (nbv < 1) nbv = 1;
-    if (nbs > partial_cap) nbs = partial_cap;
-    if (nbv > partial_cap) nbv = partial_cap;
+    d.err = h->d_err;
+    sys_partition(d, h, num_sms, resident);
+    const int64_t nbs = d.nblk_spmv, nbv = d.nblk_vec;
     if (nbs > NA_MAX_BLOCKS || nbv > NA_MAX_BLOCKS) return GSE_ERR_UNSUPPORTED;
-    d.nblk_spmv = (int)nbs;
-    d.nblk_vec = (int)nbv;
+    const int wsmem = sys_warp_smem(d);
     d.b = b;
     d.x = x;
     d.r = (double*)(base_ptr + NA_OFF_R);
@@ -187,7 +177,8 @@ extern "C" int gse_cg_noalloc(gse_handle h, const double* b, double* x, double t
     while (used < budget) {
         const int nb = budget - used < 16 ? budget - used : 16;
         for (int it = 0; it < nb; it++) {
-            k_cg_p1<<<(unsigned)nbs, 256, p1_smem(), s>>>(d_sys, map_spmv);
+            k_cg_p1<<<(unsigned)nbs, ENG_WARPS * 32, (size_t)ENG_WARPS * wsmem, s>>>(d_sys, map_spmv, wsmem);
+            k_cg_fix<<<(unsigned)nbv, 256, 0, s>>>(d_sys, map_vec);
             k_cg_p2<<<(unsigned)nbv, 256, 0, s>>>(d_sys, map_vec);
             k_cg_p3<<<(unsigned)nbv, 256, 0, s>>>(d_sys, map_vec);
         }
@@ -211,7 +202,11 @@ extern "C" int gse_cg_noalloc(gse_handle h, const double* b, double* x, double t
         true_res = sqrt(nrm2) / hs.nb;
     }
     if (cudaGetLastError() != cudaSuccess) return GSE_ERR_CUDA;
-    const int status = hs.mode == MODE_DONE ? hs.status : GSE_MAXITER;
+    int status = hs.mode == MODE_DONE ? hs.status : GSE_MAXITER;
+    int err = 0;
+    cudaMemcpyAsync(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    if (err) status = GSE_TIMEOUT;   // a bounded device-side wait gave up
     if (info) {
         memset(info, 0, sizeof(*info));
         info->status = status;

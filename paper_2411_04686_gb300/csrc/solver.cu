@@ -57,22 +57,38 @@ __device__ __forceinline__ bool sys_grid_sum(double v, double* partial, unsigned
     return true;
 }
 
-template <int UPL>
-__device__ __forceinline__ double run_chunk(int k, const MatView& m, const double* x, const Epi& e,
-                                            int64_t c, double* yb) {
+// ITER: q = A p with the p.q epilogue; RESID: y = b - A x, no dot.  The engine
+// always runs one unit of 8 nonzeros per lane (chunks of 256).
+template <bool ITER>
+__device__ __forceinline__ double eng_pipe(int k, const MatView& m, const double* x, const Epi& e, int64_t c0,
+                                           int64_t cs, int64_t nch, unsigned char* wsm, int* err) {
     switch (k) {
-        case 1: return process_chunk<1, 0, UPL>(m, x, e, c, yb);
-        case 2: return process_chunk<2, 0, UPL>(m, x, e, c, yb);
-        case 3: return process_chunk<3, -1, UPL>(m, x, e, c, yb);
-        case SRC_FP32: return process_chunk<SRC_FP32, 0, UPL>(m, x, e, c, yb);
-        default: return process_chunk<SRC_FP64, 0, UPL>(m, x, e, c, yb);
+        case 1: return spmv_warp_pipe<1, 0, 1, ITER, !ITER, ENG_STAGES>(m, x, e, c0, cs, nch, wsm, err);
+        case 2: return spmv_warp_pipe<2, 0, 1, ITER, !ITER, ENG_STAGES>(m, x, e, c0, cs, nch, wsm, err);
+        case 3: return spmv_warp_pipe<3, -1, 1, ITER, !ITER, ENG_STAGES>(m, x, e, c0, cs, nch, wsm, err);
+        case SRC_FP32: return spmv_warp_pipe<SRC_FP32, 0, 1, ITER, !ITER, ENG_STAGES>(m, x, e, c0, cs, nch, wsm, err);
+        default: return spmv_warp_pipe<SRC_FP64, 0, 1, ITER, !ITER, ENG_STAGES>(m, x, e, c0, cs, nch, wsm, err);
+    }
+}
+
+template <bool ITER>
+__device__ __forceinline__ double eng_rows(int k, const MatView& m, const double* x, const Epi& e, int64_t sb0,
+                                           int64_t sbs, int64_t nsb, int span, unsigned char* smem, int* err) {
+    switch (k) {
+        case 1: return spmv_rows_block<1, 0, ITER, !ITER, ENG_STAGES>(m, x, e, sb0, sbs, nsb, row_stage_layout<1, 0>(span, m.r_lo), smem, err);
+        case 2: return spmv_rows_block<2, 0, ITER, !ITER, ENG_STAGES>(m, x, e, sb0, sbs, nsb, row_stage_layout<2, 0>(span, m.r_lo), smem, err);
+        case 3: return spmv_rows_block<3, -1, ITER, !ITER, ENG_STAGES>(m, x, e, sb0, sbs, nsb, row_stage_layout<3, -1>(span, m.r_lo), smem, err);
+        case SRC_FP32: return spmv_rows_block<SRC_FP32, 0, ITER, !ITER, ENG_STAGES>(m, x, e, sb0, sbs, nsb, row_stage_layout<SRC_FP32, 0>(span, m.r_lo), smem, err);
+        default: return spmv_rows_block<SRC_FP64, 0, ITER, !ITER, ENG_STAGES>(m, x, e, sb0, sbs, nsb, row_stage_layout<SRC_FP64, 0>(span, m.r_lo), smem, err);
     }
 }
 
 // ---- P1: SpMV phase -------------------------------------------------------
 
-__global__ void __launch_bounds__(256) k_cg_p1(const SysDesc* __restrict__ sys, const int2* __restrict__ map) {
-    extern __shared__ double smem[];
+__global__ void __launch_bounds__(ENG_WARPS * 32) k_cg_p1(const SysDesc* __restrict__ sys,
+                                                           const int2* __restrict__ map, int warp_smem) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ double red[32];
     const int2 bm = map[blockIdx.x];
     const SysDesc& S = sys[bm.x];
     CgState* st = S.st;
@@ -90,24 +106,40 @@ __global__ void __launch_bounds__(256) k_cg_p1(const SysDesc* __restrict__ sys, 
     } else {
         e.kind = EPI_RESID; e.y = S.q; e.b = S.b; e.p = nullptr; x = S.x; k = S.prm.kmax;
     }
-    fill_empty_rows(m, e, (int64_t)lb * blockDim.x + threadIdx.x, (int64_t)nblk * blockDim.x);
     const int warp = threadIdx.x >> 5;
-    const int upl = S.upl;
-    double* yb = smem + warp * 512;
-    double* red = smem + ENG_WARPS * 512;
-    double dot = 0.0;
-    const int64_t nch = S.n_chunks;
-    if (upl == 1) {
-        for (int64_t c = (int64_t)lb * ENG_WARPS + warp; c < nch; c += (int64_t)nblk * ENG_WARPS)
-            dot += run_chunk<1>(k, m, x, e, c, yb);
-    } else {
-        for (int64_t c = (int64_t)lb * ENG_WARPS + warp; c < nch; c += (int64_t)nblk * ENG_WARPS)
-            dot += run_chunk<2>(k, m, x, e, c, yb);
-    }
+    unsigned char* wsm = smem + warp * warp_smem;
+    const int64_t c0 = (int64_t)lb * ENG_WARPS + warp, cs = (int64_t)nblk * ENG_WARPS;
+    const bool rows = S.sched == GSE_SCHEDULE_ROWS;
+    const int64_t nsb = (S.n + 32 * ENG_WARPS - 1) / (32 * ENG_WARPS);
+    if (!rows) fill_empty_rows(m, e, (int64_t)lb * blockDim.x + threadIdx.x, (int64_t)nblk * blockDim.x);
     if (mode == MODE_ITER) {
+        const double dot = rows ? eng_rows<true>(k, m, x, e, lb, nblk, nsb, S.row_span, smem, S.err)
+                                : eng_pipe<true>(k, m, x, e, c0, cs, S.n_chunks, wsm, S.err);
         double total;
         if (sys_grid_sum(dot, S.partial, S.counter, lb, nblk, red, &total) && threadIdx.x == 0) st->pq = total;
+    } else {
+        if (rows) eng_rows<false>(k, m, x, e, lb, nblk, nsb, S.row_span, smem, S.err);
+        else eng_pipe<false>(k, m, x, e, c0, cs, S.n_chunks, wsm, S.err);
     }
+}
+
+// ---- P1b: rows that cross chunks (after P1) --------------------------------
+
+__global__ void __launch_bounds__(256) k_cg_fix(const SysDesc* __restrict__ sys, const int2* __restrict__ map) {
+    const int2 bm = map[blockIdx.x];
+    const SysDesc& S = sys[bm.x];
+    const int mode = S.st->mode;
+    if (mode == MODE_DONE || S.n_chunks < 2 || S.sched == GSE_SCHEDULE_ROWS) return;
+    Epi e;
+    if (mode == MODE_ITER) {
+        e.kind = EPI_CG_PQ; e.y = S.q; e.b = nullptr; e.p = S.p;
+    } else {
+        e.kind = EPI_RESID; e.y = mode == MODE_RESID_R ? S.r : S.q; e.b = S.b; e.p = nullptr;
+    }
+    const MatView m = S.m;
+    const int64_t tid = (int64_t)bm.y * blockDim.x + threadIdx.x, nt = (int64_t)S.nblk_vec * blockDim.x;
+    if (S.upl == 1) fix_split_rows<256>(m, e, S.n_chunks, tid, nt);
+    else fix_split_rows<512>(m, e, S.n_chunks, tid, nt);
 }
 
 // ---- P2: residual update, history, policy, next mode ----------------------
@@ -479,6 +511,7 @@ struct gse_cg_engine {
     int2* d_map_vec = nullptr;
     int map_cap_spmv = 0, map_cap_vec = 0;
     int nblk_spmv = 0, nblk_vec = 0;
+    int warp_smem = 0;
     std::vector<EngineSlot> slots;
     std::vector<SysDesc> h_sys;
     bool dirty = true;
@@ -494,9 +527,10 @@ extern "C" int gse_engine_create(int capacity, void* stream, gse_engine* out) {
     e->stream = (cudaStream_t)stream;
     cudaGetDevice(&e->device);
     cudaDeviceGetAttribute(&e->num_sms, cudaDevAttrMultiProcessorCount, e->device);
-    cudaFuncSetAttribute((const void*)k_cg_p1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p1_smem());
+    cudaFuncSetAttribute((const void*)k_cg_p1, cudaFuncAttributeMaxDynamicSharedMemorySize, ENG_WARPS * eng_max_warp_smem());
     int nb = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cg_p1, 256, p1_smem()) != cudaSuccess || nb < 1) nb = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cg_p1, ENG_WARPS * 32, p1_smem()) != cudaSuccess || nb < 1)
+        nb = 1;
     e->p1_resident = nb;
     e->slots.resize(capacity);
     e->h_sys.resize(capacity);
@@ -562,20 +596,9 @@ extern "C" int gse_engine_submit(gse_engine e, gse_handle h, const double* b, do
     SysDesc d;
     memset(&d, 0, sizeof(d));
     d.m = h->v;
-    d.upl = units_per_lane(h) >= 2 ? 2 : 1;
-    d.n = h->v.n_rows;
-    d.n_chunks = (h->v.nnz + 256 * d.upl - 1) / (256 * d.upl);
-    int64_t nbs = (d.n_chunks + ENG_WARPS - 1) / ENG_WARPS;
-    const int64_t cap_s = (int64_t)e->num_sms * e->p1_resident;
-    if (nbs > cap_s) nbs = cap_s;
-    if (nbs < 1) nbs = 1;
-    int64_t nbv = (d.n + 1023) / 1024;
-    if (nbv > (int64_t)e->num_sms * 8) nbv = (int64_t)e->num_sms * 8;
-    if (nbv < 1) nbv = 1;
-    if (nbs > w->partial_cap) nbs = w->partial_cap;
-    if (nbv > w->partial_cap) nbv = w->partial_cap;
-    d.nblk_spmv = (int)nbs;
-    d.nblk_vec = (int)nbv;
+    d.err = h->d_err;
+    sys_partition(d, h, e->num_sms, e->p1_resident);
+    if (d.nblk_spmv > w->partial_cap || d.nblk_vec > w->partial_cap) return GSE_ERR_INVALID;
     d.b = b;
     d.x = x;
     d.r = w->r;
@@ -622,9 +645,11 @@ extern "C" int gse_engine_submit(gse_engine e, gse_handle h, const double* b, do
 
 static int rebuild_maps(gse_cg_engine* e) {
     std::vector<int2> ms, mv;
+    int wsm = ENG_WARP_SMEM;
     for (int i = 0; i < e->capacity; i++) {
         if (!e->slots[i].active) continue;
         const SysDesc& d = e->h_sys[i];
+        if (sys_warp_smem(d) > wsm) wsm = sys_warp_smem(d);
         for (int b = 0; b < d.nblk_spmv; b++) ms.push_back(make_int2(i, b));
         for (int b = 0; b < d.nblk_vec; b++) mv.push_back(make_int2(i, b));
     }
@@ -644,13 +669,16 @@ static int rebuild_maps(gse_cg_engine* e) {
     if (!mv.empty()) cudaMemcpy(e->d_map_vec, mv.data(), mv.size() * sizeof(int2), cudaMemcpyHostToDevice);
     e->nblk_spmv = (int)ms.size();
     e->nblk_vec = (int)mv.size();
+    e->warp_smem = wsm;
     e->dirty = false;
     return GSE_OK;
 }
 
 static void enqueue_slots(gse_cg_engine* e, int nslots) {
     for (int it = 0; it < nslots; it++) {
-        k_cg_p1<<<e->nblk_spmv, 256, p1_smem(), e->stream>>>(e->d_sys, e->d_map_spmv);
+        k_cg_p1<<<e->nblk_spmv, ENG_WARPS * 32, (size_t)ENG_WARPS * e->warp_smem, e->stream>>>(e->d_sys, e->d_map_spmv,
+                                                                                             e->warp_smem);
+        k_cg_fix<<<e->nblk_vec, 256, 0, e->stream>>>(e->d_sys, e->d_map_vec);
         k_cg_p2<<<e->nblk_vec, 256, 0, e->stream>>>(e->d_sys, e->d_map_vec);
         k_cg_p3<<<e->nblk_vec, 256, 0, e->stream>>>(e->d_sys, e->d_map_vec);
     }
@@ -714,6 +742,9 @@ extern "C" int gse_engine_run(gse_engine e, int max_slots, int batch, int* n_run
 static void fill_info(gse_cg_engine* e, int slot, gse_solve_info* info, double rel_true) {
     const CgState& s = e->h_state[slot];
     info->status = s.mode == MODE_DONE ? s.status : GSE_MAXITER;
+    int err = 0;
+    cudaMemcpy(&err, e->slots[slot].h->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (err) info->status = GSE_TIMEOUT;   // a bounded device-side wait gave up
     info->iters = s.j < 0 ? 0 : s.j;
     const int base = e->h_sys[slot].prm.kmax > 3;
     info->k_final = base ? 0 : s.k;

@@ -1,148 +1,176 @@
 // spmv.cu -- standalone GSE-SpMV (gse_spmv) and the plain FP64 / FP32 CSR
-// baselines through the same chunk engine; schedule choice and autotuning.
+// baselines through the same TMA-staged chunk loop; schedule choice and
+// autotuning.
 #include <cstdio>
 #include <mutex>
 
-#include "spmv_core.cuh"
+#include "spmv_pipe.cuh"
 
 namespace gse {
 
-constexpr int SPMV_WARPS = 8;
-
-template <int UPL>
-constexpr size_t spmv_smem() { return (size_t)SPMV_WARPS * 256 * UPL * sizeof(double) + 64 * sizeof(double); }
-
-// Reduces one double per block (v, valid in thread 0) over the grid into
-// *out; the last block to finish sums the block partials in block order.
-__device__ __forceinline__ void grid_sum_last_block(double v, double* partial, unsigned* counter,
-                                                    double* out, double* red) {
-    __shared__ bool last;
-    if (threadIdx.x == 0) {
-        partial[blockIdx.x] = v;
-        __threadfence();
-        last = atomicAdd(counter, 1u) == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    double s = 0.0;
-    for (unsigned i = threadIdx.x; i < gridDim.x; i += blockDim.x) s += __ldcg(partial + i);
-    s = block_sum(s, red);
-    if (threadIdx.x == 0) {
-        *out = s;
-        *counter = 0;
-    }
-}
+constexpr int SPMV_WARPS = 4;
+constexpr int SPMV_STAGES = 3;
 
 template <int K, int R, int UPL>
-__global__ void __launch_bounds__(256) k_spmv(MatView m, const double* __restrict__ x, Epi e,
-                                               int64_t n_chunks, double* red_partial,
-                                               unsigned* red_counter, double* dot_out, const int* gate) {
+constexpr size_t spmv_smem() { return (size_t)SPMV_WARPS * warp_smem_bytes<K, R, UPL, SPMV_STAGES>(); }
+
+// y = A_k x (or b - A_k x): every warp runs spmv_warp_pipe over its chunks.
+template <int K, int R, int UPL, bool RESID>
+__global__ void __launch_bounds__(SPMV_WARPS * 32) k_spmv(MatView m, const double* __restrict__ x, Epi e,
+                                                           int64_t n_chunks, int* err, const int* gate) {
     if (gate && *gate) return;
-    extern __shared__ double smem[];
-    constexpr int CH = 256 * UPL;
+    extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5;
-    double* yb = smem + warp * CH;
-    double* red = smem + SPMV_WARPS * CH;
-    fill_empty_rows(m, e, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
-                    (int64_t)gridDim.x * blockDim.x);
-    double dot = 0.0;
-    for (int64_t c = (int64_t)blockIdx.x * SPMV_WARPS + warp; c < n_chunks;
-         c += (int64_t)gridDim.x * SPMV_WARPS)
-        dot += process_chunk<K, R, UPL>(m, x, e, c, yb);
-    if (e.kind == EPI_CG_PQ) {
-        const double s = block_sum(dot, red);
-        grid_sum_last_block(s, red_partial, red_counter, dot_out, red);
-    }
+    fill_empty_rows(m, e, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
+    spmv_warp_pipe<K, R, UPL, false, RESID, SPMV_STAGES>(
+        m, x, e, (int64_t)blockIdx.x * SPMV_WARPS + warp, (int64_t)gridDim.x * SPMV_WARPS, n_chunks,
+        smem + warp * warp_smem_bytes<K, R, UPL, SPMV_STAGES>(), err);
 }
 
-typedef void (*SpmvKernel)(MatView, const double*, Epi, int64_t, double*, unsigned*, double*, const int*);
-
-template <int K, int R, int UPL>
-SpmvKernel kernel_of() { return k_spmv<K, R, UPL>; }
-
-template <int K, int R>
-SpmvKernel pick_upl(int upl) {
-    switch (upl) {
-        case 1: return kernel_of<K, R, 1>();
-        case 2: return kernel_of<K, R, 2>();
-        default: return kernel_of<K, R, 4>();
-    }
+// Finishes the rows that cross chunk boundaries (after k_spmv, same stream).
+template <int UPL>
+__global__ void __launch_bounds__(256) k_spmv_fix(MatView m, Epi e, int64_t n_chunks, const int* gate) {
+    if (gate && *gate) return;
+    fix_split_rows<256 * UPL>(m, e, n_chunks, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                              (int64_t)gridDim.x * blockDim.x);
 }
 
-static SpmvKernel pick_kernel(int k, int r_lo, int upl) {
+// Row schedule: one row per lane, 256 consecutive rows per CTA and stage,
+// staged by one producer thread with large bulk copies (short rows).
+constexpr int ROWS_WARPS = 8;
+constexpr int ROWS_STAGES = 3;
+
+template <int K, int R, bool RESID>
+__global__ void __launch_bounds__(ROWS_WARPS * 32) k_spmv_rows(MatView m, const double* __restrict__ x, Epi e,
+                                                                int64_t nsb, RowStage L, int* err, const int* gate) {
+    if (gate && *gate) return;
+    extern __shared__ __align__(128) unsigned char smem[];
+    spmv_rows_block<K, R, false, RESID, ROWS_STAGES>(m, x, e, blockIdx.x, gridDim.x, nsb, L, smem, err);
+}
+
+typedef void (*RowsKernel)(MatView, const double*, Epi, int64_t, RowStage, int*, const int*);
+
+template <bool RESID>
+static RowsKernel pick_rows_t(int k, int r_lo, RowStage* L, int span) {
     switch (k) {
-        case 1: return pick_upl<1, 0>(upl);
-        case 2: return pick_upl<2, 0>(upl);
+        case 1: *L = row_stage_layout<1, 0>(span, r_lo); return k_spmv_rows<1, 0, RESID>;
+        case 2: *L = row_stage_layout<2, 0>(span, r_lo); return k_spmv_rows<2, 0, RESID>;
+        case 3: *L = row_stage_layout<3, -1>(span, r_lo); return k_spmv_rows<3, -1, RESID>;
+        case SRC_FP32: *L = row_stage_layout<SRC_FP32, 0>(span, r_lo); return k_spmv_rows<SRC_FP32, 0, RESID>;
+        default: *L = row_stage_layout<SRC_FP64, 0>(span, r_lo); return k_spmv_rows<SRC_FP64, 0, RESID>;
+    }
+}
+
+static int launch_rows(gse_matrix* h, int k, int epi, const SpmvArgs& a, cudaStream_t s) {
+    RowStage L;
+    const bool resid = epi == EPI_RESID;
+    RowsKernel fn = resid ? pick_rows_t<true>(k, h->v.r_lo, &L, h->row_span256)
+                          : pick_rows_t<false>(k, h->v.r_lo, &L, h->row_span256);
+    const size_t smem = (size_t)rows_block_smem<ROWS_STAGES>(L);
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute((const void*)fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, ROWS_WARPS * 32, smem) != cudaSuccess || nb < 1) nb = 1;
+    const int64_t nsb = (h->v.n_rows + 32 * ROWS_WARPS - 1) / (32 * ROWS_WARPS);
+    int64_t g = nsb;
+    const int64_t resident = (int64_t)h->num_sms * nb;
+    if (g > resident) g = resident;
+    if (g < 1) g = 1;
+    Epi e;
+    e.kind = epi;
+    e.y = a.y;
+    e.b = a.b;
+    e.p = a.p;
+    fn<<<(unsigned)g, ROWS_WARPS * 32, smem, s>>>(h->v, a.x, e, nsb, L, h->d_err, a.skip_flag);
+    return cudaGetLastError() == cudaSuccess ? GSE_OK : GSE_ERR_CUDA;
+}
+
+typedef void (*SpmvKernel)(MatView, const double*, Epi, int64_t, int*, const int*);
+
+struct KernelPick {
+    SpmvKernel fn;
+    size_t smem;
+};
+
+template <int K, int R, bool RESID>
+KernelPick pick_upl(int upl) {
+    switch (upl) {
+        case 1: return {k_spmv<K, R, 1, RESID>, spmv_smem<K, R, 1>()};
+        case 2: return {k_spmv<K, R, 2, RESID>, spmv_smem<K, R, 2>()};
+        default: return {k_spmv<K, R, 4, RESID>, spmv_smem<K, R, 4>()};
+    }
+}
+
+template <bool RESID>
+static KernelPick pick_kernel_t(int k, int r_lo, int upl) {
+    switch (k) {
+        case 1: return pick_upl<1, 0, RESID>(upl);
+        case 2: return pick_upl<2, 0, RESID>(upl);
         case 3:
             switch (r_lo) {
-                case 0: return pick_upl<3, 0>(upl);
-                case 4: return pick_upl<3, 4>(upl);
-                case 8: return pick_upl<3, 8>(upl);
-                default: return pick_upl<3, 16>(upl);
+                case 0: return pick_upl<3, 0, RESID>(upl);
+                case 4: return pick_upl<3, 4, RESID>(upl);
+                case 8: return pick_upl<3, 8, RESID>(upl);
+                default: return pick_upl<3, 16, RESID>(upl);
             }
-        case SRC_FP32: return pick_upl<SRC_FP32, 0>(upl);
-        default: return pick_upl<SRC_FP64, 0>(upl);
+        case SRC_FP32: return pick_upl<SRC_FP32, 0, RESID>(upl);
+        default: return pick_upl<SRC_FP64, 0, RESID>(upl);
     }
 }
 
-static size_t smem_of(int upl) {
-    return upl == 1 ? spmv_smem<1>() : upl == 2 ? spmv_smem<2>() : spmv_smem<4>();
+static KernelPick pick_kernel(int k, int r_lo, int upl, bool resid) {
+    return resid ? pick_kernel_t<true>(k, r_lo, upl) : pick_kernel_t<false>(k, r_lo, upl);
 }
 
 // Occupancy-derived resident blocks per SM for each kernel (cached).
-static int resident_blocks(SpmvKernel kfn, int upl) {
+static int resident_blocks(const KernelPick& kp) {
     static std::mutex mu;
-    static const void* keys[64];
-    static int vals[64];
+    static const void* keys[128];
+    static int vals[128];
     static int nkeys = 0;
     std::lock_guard<std::mutex> lock(mu);
     for (int i = 0; i < nkeys; i++)
-        if (keys[i] == (const void*)kfn) return vals[i];
-    const size_t sm = smem_of(upl);
-    if (sm > 48 * 1024)
-        cudaFuncSetAttribute((const void*)kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (keys[i] == (const void*)kp.fn) return vals[i];
+    if (kp.smem > 48 * 1024)
+        cudaFuncSetAttribute((const void*)kp.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kp.smem);
+    cudaFuncSetAttribute((const void*)kp.fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kfn, 256, sm) != cudaSuccess || nb < 1) nb = 1;
-    if (nkeys < 64) {
-        keys[nkeys] = (const void*)kfn;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kp.fn, SPMV_WARPS * 32, kp.smem) != cudaSuccess || nb < 1)
+        nb = 1;
+    if (nkeys < 128) {
+        keys[nkeys] = (const void*)kp.fn;
         vals[nkeys] = nb;
         nkeys++;
     }
     return nb;
 }
 
-int spmv_grid(gse_matrix* h, int upl) {
-    const int64_t ch = 256 * upl;
-    const int64_t n_chunks = (h->v.nnz + ch - 1) / ch;
-    SpmvKernel kfn = pick_kernel(3, h->v.r_lo, upl);
-    const int64_t resident = (int64_t)h->num_sms * resident_blocks(kfn, upl);
-    int64_t g = (n_chunks + SPMV_WARPS - 1) / SPMV_WARPS;
-    if (g > resident) g = resident;
-    if (g < 1) g = 1;
-    return (int)g;
-}
-
 int launch_spmv(gse_matrix* h, int k, int epi, const SpmvArgs& a, cudaStream_t s, int upl_override) {
     const int upl = upl_override ? upl_override : units_per_lane(h);
-    SpmvKernel kfn = pick_kernel(k, h->v.r_lo, upl);
+    if (upl == GSE_SCHEDULE_ROWS) return launch_rows(h, k, epi, a, s);
+    const KernelPick kp = pick_kernel(k, h->v.r_lo, upl, epi == EPI_RESID);
     const int64_t ch = 256 * upl;
     const int64_t n_chunks = (h->v.nnz + ch - 1) / ch;
-    const int64_t resident = (int64_t)h->num_sms * resident_blocks(kfn, upl);
+    const int64_t resident = (int64_t)h->num_sms * resident_blocks(kp);
     int64_t g = (n_chunks + SPMV_WARPS - 1) / SPMV_WARPS;
     if (g > resident) g = resident;
-    const int64_t gmin = (h->v.n_empty + 255) / 256;
+    const int64_t gmin = (h->v.n_empty + SPMV_WARPS * 32 - 1) / (SPMV_WARPS * 32);
     if (g < gmin) g = gmin < resident ? gmin : resident;
     if (g < 1) g = 1;
-    if (epi == EPI_CG_PQ && g > h->red_capacity) g = h->red_capacity;
     Epi e;
     e.kind = epi;
     e.y = a.y;
     e.b = a.b;
     e.p = a.p;
-    kfn<<<(unsigned)g, 256, smem_of(upl), s>>>(h->v, a.x, e, n_chunks, a.red_partial ? a.red_partial : h->red_partial,
-                                              a.red_counter ? a.red_counter : h->red_counter, a.dot_out,
-                                              a.skip_flag);
+    kp.fn<<<(unsigned)g, SPMV_WARPS * 32, kp.smem, s>>>(h->v, a.x, e, n_chunks, h->d_err, a.skip_flag);
+    if (n_chunks > 1) {
+        int64_t gf = (n_chunks + 255) / 256;
+        if (gf > (int64_t)h->num_sms * 8) gf = (int64_t)h->num_sms * 8;
+        if (upl == 1) k_spmv_fix<1><<<(unsigned)gf, 256, 0, s>>>(h->v, e, n_chunks, a.skip_flag);
+        else if (upl == 2) k_spmv_fix<2><<<(unsigned)gf, 256, 0, s>>>(h->v, e, n_chunks, a.skip_flag);
+        else k_spmv_fix<4><<<(unsigned)gf, 256, 0, s>>>(h->v, e, n_chunks, a.skip_flag);
+    }
     return cudaGetLastError() == cudaSuccess ? GSE_OK : GSE_ERR_CUDA;
 }
 
@@ -166,7 +194,9 @@ extern "C" int gse_spmv(gse_handle h, int k, const double* x, double* y, void* s
 }
 
 extern "C" int gse_set_schedule(gse_handle h, int upl) {
-    if (!h || !(upl == 0 || upl == 1 || upl == 2 || upl == 4)) return GSE_ERR_INVALID;
+    if (!h || !(upl == 0 || upl == 1 || upl == 2 || upl == 4 || upl == GSE_SCHEDULE_ROWS)) return GSE_ERR_INVALID;
+    if (upl == GSE_SCHEDULE_ROWS && (h->row_span256 > GSE_ROW_SPAN_MAX || h->row_span128 > GSE_ROW_SPAN_MAX))
+        return GSE_ERR_UNSUPPORTED;
     h->schedule_forced = upl;
     return GSE_OK;
 }
@@ -184,14 +214,16 @@ extern "C" int gse_autotune(gse_handle h, int k, void* stream) {
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    const int cands[3] = {1, 2, 4};
+    const int cands[4] = {GSE_SCHEDULE_ROWS, 1, 2, 4};
     float best = 1e30f;
     int best_upl = units_per_lane(h);
     SpmvArgs a = {};
     a.x = x;
     a.y = y;
-    for (int ci = 0; ci < 3; ci++) {
+    for (int ci = 0; ci < 4; ci++) {
         const int upl = cands[ci];
+        if (upl == GSE_SCHEDULE_ROWS && (h->row_span256 > GSE_ROW_SPAN_MAX || h->row_span128 > GSE_ROW_SPAN_MAX))
+            continue;
         launch_spmv(h, k, EPI_STORE, a, s, upl);  // warm
         cudaEventRecord(e0, s);
         for (int r = 0; r < 5; r++) launch_spmv(h, k, EPI_STORE, a, s, upl);

@@ -1,19 +1,18 @@
-// spmv_core.cuh -- the GSE-SpMV chunk engine (Sec. III-C, Alg. 2 and its tail
-// variants), shared by the standalone SpMV and the solver kernels.
+// spmv_core.cuh -- building blocks of the GSE-SpMV (Sec. III-C, Alg. 2 and its
+// tail variants): the integer-only decoders, value loads, epilogues and the pass
+// that finishes rows crossing chunks.  The main loop is in spmv_pipe.cuh.
 //
 // Schedule: nonzero-split.  A chunk is CH = 256 * UPL consecutive nonzeros,
 // processed by one warp; lane l owns UPL consecutive units of 8 nonzeros.  Each
-// lane loads its segment words, column indices and row-end bits with 128-bit
-// loads, rebuilds each value in registers with integer operations only (leading
-// one by CLZ, exponent from the group exponent, mantissa by shifts; no
-// int->double conversion and no FP64 scaling), gathers x[col] through L1/L2 and
-// accumulates with exactly one DFMA per nonzero.  Rows that end inside a lane
-// are finished there; a row that crosses lanes is stitched by a segmented warp
-// scan of the lane carries (skipped when every lane sees a row end, which holds
-// whenever rows are at most 8 long); a row that crosses chunks is combined
-// through per-chunk scratch by the last of its chunks to finish (fixed summation
-// order, so results are deterministic).  Finished rows are staged in shared
-// memory and written back coalesced, through an epilogue.
+// value is rebuilt in registers with integer operations only (leading one by
+// CLZ, exponent from the group exponent, mantissa by shifts; no int->double
+// conversion and no FP64 scaling) and accumulated with exactly one DFMA.  Rows
+// that end inside a lane are finished there; a row that crosses lanes is
+// stitched by a segmented warp scan of the lane carries (skipped when every lane
+// sees a row end, which holds whenever rows are at most 8 long); a row that
+// crosses chunks leaves one piece per chunk in scratch and is summed, in chunk
+// order, by fix_split_rows after the SpMV (deterministic).  Finished rows are
+// staged in shared memory and written back coalesced, through an epilogue.
 #pragma once
 
 #include "gse_internal.cuh"
@@ -41,6 +40,20 @@ __device__ __forceinline__ double decode_l1(uint32_t h, int Eg, const MatView& m
     if (mag != 0 && expo <= 0) return decode_tiny(mag, Eg, m.W1, sign);
     const uint32_t hi = (sign << 31) | ((uint32_t)expo << 20) | ((mag << (lz - 11)) & 0xFFFFFu);
     return __hiloint2double((int)(mag ? hi : (sign << 31)), 0);
+}
+
+// Level 1 for the row schedule: the leading one and the shifted mantissa come
+// from the FP32 image of M_1 (exact: M_1 < 2^24, built by integer insertion and
+// one FP32 subtraction), so the FP64 high word is that image shifted right by 3
+// plus an exponent offset.  eoff = (E_g - W_1 - 127) << 20, per group.
+__device__ __forceinline__ double decode_l1_f(uint32_t h, int Eg, uint32_t eoff, const MatView& m) {
+    const uint32_t mag = h & ((1u << m.W1) - 1u);
+    const uint32_t sign = (h >> m.W1) << 31;
+    const float f = __uint_as_float(0x4B000000u | mag) - 8388608.0f;   // == (float)mag
+    const uint32_t fb = __float_as_uint(f);
+    if (mag != 0 && Eg <= m.W1) return decode_tiny(mag, Eg, m.W1, sign >> 31);
+    const uint32_t hi = mag ? ((fb >> 3) + eoff) | sign : sign;
+    return __hiloint2double((int)hi, 0);
 }
 
 // Level 2: M_2 = head magnitude << s2 | tail1 (W_2 <= 31 bits).
@@ -167,146 +180,41 @@ __device__ __forceinline__ void epi_finish(const Epi& e, int64_t R, double v) {
     else e.y[R] = v;
 }
 
+// Same, with the kind fixed at compile time (no predicated-off FP64 work).
+template <bool RESID>
+__device__ __forceinline__ void epi_finish_t(const Epi& e, int64_t R, double v) {
+    if constexpr (RESID) e.y[R] = e.b[R] - v;
+    else e.y[R] = v;
+}
+
 // Maps a compact (nonempty) row index to the matrix row.
 __device__ __forceinline__ int64_t actual_row(const MatView& m, int64_t rc) {
     return m.nzrow ? (int64_t)__ldg(m.nzrow + rc) : rc;
 }
 
-// Adds `piece` of row R (a row crossing chunks) to the chunk scratch; the last
-// chunk of the row to arrive sums the pieces in chunk order and finishes it.
-// first: this chunk holds the row's first nonzero.
+// Rows that cross chunk boundaries.  A chunk stores the piece of the row that
+// was open when it began in part[c] (only if it began mid-row) and the piece of
+// the row still open at its end in carry[c] (only if that row began inside it).
+// fix_split_rows (a separate, later pass) adds carry[c1] + part[c1+1..c2] in
+// chunk order for every such row: deterministic, and no fences or atomics in
+// the SpMV itself.
 template <int CH>
-__device__ __noinline__ void combine_split(const MatView& m, const Epi& e, int64_t c, int64_t R,
-                                           double piece, bool first) {
-    if (first) m.carry[c] = piece;
-    else m.part[c] = piece;
-    const int64_t s = __ldg(m.row_ptr + R), t = __ldg(m.row_ptr + R + 1);
-    const int64_t c1 = s / CH, c2 = (t - 1) / CH;
-    __threadfence();
-    const int old = atomicAdd(m.cnt + c1, 1);
-    if (old == (int)(c2 - c1)) {
-        __threadfence();
-        double sum = __ldcg(m.carry + c1);
-        for (int64_t cc = c1 + 1; cc <= c2; cc++) sum += __ldcg(m.part + cc);
-        epi_finish(e, R, sum);
-        atomicExch(m.cnt + c1, 0);
-    }
-}
-
-// Processes chunk c (CH = 256 * UPL nonzeros) with one warp.  yb: this warp's
-// shared staging buffer of CH doubles.  Returns the lane's dot contribution
-// (EPI_CG_PQ), else 0.
-template <int K, int R, int UPL>
-__device__ __forceinline__ double process_chunk(const MatView& m, const double* __restrict__ x,
-                                                const Epi& e, int64_t c, double* yb) {
-    constexpr int CH = 256 * UPL;
-    const unsigned FULL = 0xFFFFFFFFu;
-    const int lane = threadIdx.x & 31;
-    const int64_t u0 = c * (32 * UPL) + (int64_t)lane * UPL;   // first unit of the lane
-
-    // row-end bits of the lane's 8*UPL nonzeros
-    const uint32_t wbits = __ldg(m.rowend + (u0 >> 2));
-    uint32_t bits;
-    if constexpr (UPL == 4) bits = wbits;
-    else if constexpr (UPL == 2) bits = (wbits >> ((u0 & 3) * 8)) & 0xFFFFu;
-    else bits = (wbits >> ((u0 & 3) * 8)) & 0xFFu;
-    const int cnt = __popc(bits);
-    int incl = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(FULL, incl, o);
-        if (lane >= o) incl += t;
-    }
-    const int excl = incl - cnt;
-    const int total_ends = __shfl_sync(FULL, incl, 31);
-    const int64_t row0 = __ldg(m.blk_row0 + c * UPL);
-    bool starts_mid = false;
-    if (c > 0) {
+__device__ __forceinline__ void fix_split_rows(const MatView& m, const Epi& e, int64_t n_chunks,
+                                               int64_t tid, int64_t nthreads) {
+    for (int64_t c = tid + 1; c < n_chunks; c += nthreads) {
         const int64_t pe = c * CH - 1;
-        starts_mid = !((__ldg(m.rowend + (pe >> 5)) >> (pe & 31)) & 1u);
+        if ((__ldg(m.rowend + (pe >> 5)) >> (pe & 31)) & 1u) continue;   // boundary on a row end
+        const int64_t rc = __ldg(m.blk_row0 + c * (CH / 256));
+        if (rc >= m.n_nonempty) continue;
+        const int64_t R = actual_row(m, rc);
+        const int64_t s = __ldg(m.row_ptr + R), t = __ldg(m.row_ptr + R + 1);
+        const int64_t c2 = (t - 1) / CH;
+        if (c2 != c) continue;            // a later boundary finishes this row
+        const int64_t c1 = s / CH;
+        double sum = m.carry[c1];
+        for (int64_t cc = c1 + 1; cc <= c2; cc++) sum += m.part[cc];
+        epi_finish(e, R, sum);
     }
-
-    double cur = 0.0, hp = 0.0;
-    int j = 0;
-#pragma unroll
-    for (int q = 0; q < UPL; q++) {
-        int col[8];
-        double a[8];
-        load_unit<K, R>(m, u0 + q, col, a);
-        double xv[8];
-#pragma unroll
-        for (int i = 0; i < 8; i++) xv[i] = __ldg(x + col[i]);
-#pragma unroll
-        for (int i = 0; i < 8; i++) {
-            cur = fma(a[i], xv[i], cur);
-            if ((bits >> (q * 8 + i)) & 1u) {
-                if (j == 0) hp = cur;
-                else yb[excl + j] = cur;
-                j++;
-                cur = 0.0;
-            }
-        }
-    }
-    const bool seen = j > 0;
-    const double co = cur;
-    double out, in;
-    if (__all_sync(FULL, seen)) {
-        out = co;
-    } else {
-        // segmented inclusive scan: out_i = co_i + (seen_i ? 0 : out_{i-1})
-        double v = co;
-        bool f = seen;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const double vu = __shfl_up_sync(FULL, v, o);
-            const bool fu = __shfl_up_sync(FULL, (int)f, o) != 0;
-            if (lane >= o) {
-                if (!f) v += vu;
-                f = f || fu;
-            }
-        }
-        out = v;
-    }
-    in = __shfl_up_sync(FULL, out, 1);
-    if (lane == 0) in = 0.0;
-    if (seen) yb[excl] = in + hp;
-    const double out31 = __shfl_sync(FULL, out, 31);
-    const bool last_end = __shfl_sync(FULL, (bits >> (8 * UPL - 1)) & 1u, 31) != 0;
-    __syncwarp();
-
-    double dot = 0.0;
-    // finished rows of this chunk, coalesced
-    for (int idx = lane; idx < total_ends; idx += 32) {
-        if (idx == 0 && starts_mid) continue;
-        const int64_t Rw = actual_row(m, row0 + idx);
-        const double v = yb[idx];
-        if (e.kind == EPI_CG_PQ) dot = fma(__ldg(e.p + Rw), v, dot);
-        epi_finish(e, Rw, v);
-    }
-    // rows crossing the chunk boundary
-    if (lane == 0) {
-        if (total_ends == 0) {
-            if (row0 < m.n_nonempty) {
-                const int64_t Rw = actual_row(m, row0);
-                if (e.kind == EPI_CG_PQ) dot = fma(__ldg(e.p + Rw), out31, dot);
-                combine_split<CH>(m, e, c, Rw, out31, !starts_mid);
-            }
-        } else {
-            if (starts_mid) {
-                const int64_t Rw = actual_row(m, row0);
-                if (e.kind == EPI_CG_PQ) dot = fma(__ldg(e.p + Rw), yb[0], dot);
-                combine_split<CH>(m, e, c, Rw, yb[0], false);
-            }
-            const int64_t ro = row0 + total_ends;
-            if (!last_end && ro < m.n_nonempty) {
-                const int64_t Rw = actual_row(m, ro);
-                if (e.kind == EPI_CG_PQ) dot = fma(__ldg(e.p + Rw), out31, dot);
-                combine_split<CH>(m, e, c, Rw, out31, true);
-            }
-        }
-    }
-    __syncwarp();
-    return dot;
 }
 
 // Zero rows (every SpMV writes them: y = 0, or y = b for the residual form).

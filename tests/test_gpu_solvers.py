@@ -147,3 +147,19 @@ def test_engine_continuous_batching_matches_solo():
         assert results[i]["status"] == gse.OK
         assert results[i]["iters"] == i1["iters"]
         assert torch.equal(xs[i], x1)
+
+
+@pytest.mark.parametrize("sched", [1, gse.SCHEDULE_ROWS])
+def test_stepped_cg_on_each_engine_schedule(sched):
+    """The engine's SpMV phase runs either schedule; both reach the same answer."""
+    A = synth.laplace3d(12, shift=1e-2).scaled(1.0 / 3.0)
+    M = gse.GseMatrix.from_csr(A)
+    M.set_schedule(sched)
+    b = torch.from_numpy(synth.rhs_ones(A)).cuda()
+    x = torch.zeros(A.n_rows, dtype=torch.float64, device="cuda")
+    info = M.cg(b, x, tol=1e-10, policy=gse.SCALED_CG)
+    ref = oracle.stepped_cg(A.row_ptr, A.col, oracle.levels(A.val), synth.rhs_ones(A), tol=1e-10,
+                            policy=oracle.SCALED_CG)
+    assert info["status"] == gse.OK and info["k_final"] == 3 and info["rel_res_true"] < 1e-10
+    assert abs(info["iters"] - ref["info"]["iters"]) <= 3
+    assert np.max(np.abs(x.cpu().numpy() - ref["x"])) < 1e-8

@@ -52,10 +52,21 @@ MATS = {
 
 
 @pytest.mark.parametrize("name", list(MATS))
-@pytest.mark.parametrize("upl", [1, 2, 4])
+@pytest.mark.parametrize("upl", [1, 2, 4, gse.SCHEDULE_ROWS])
 def test_spmv_levels_against_oracle(name, upl):
     A = MATS[name]()
     M = gse.GseMatrix.from_csr(A, attach=(64, 32))
+    if upl == gse.SCHEDULE_ROWS:
+        span = 0
+        for rb in (128, 256):            # row blocks of the engine's and the SpMV's CTAs
+            blocks = A.row_ptr[np.minimum(np.arange(0, A.n_rows + rb, rb), A.n_rows)].astype(np.int64)
+            if A.n_rows:
+                span = max(span, int(np.max((((blocks[1:] + 31) >> 5) << 5) - ((blocks[:-1] >> 5) << 5))))
+        if span > 4096:                  # a row block too wide for the row schedule
+            with pytest.raises(gse.GseError) as e:
+                M.set_schedule(upl)
+            assert e.value.code == gse.ERR_UNSUPPORTED
+            return
     M.set_schedule(upl)
     x = synth.uniform_x(A.n_cols, seed=3)
     xd = torch.from_numpy(x).cuda()
@@ -90,6 +101,7 @@ def test_full_size_sampled_rows(which):
     benchmark times: 4000 sampled rows checked against the oracle."""
     A = synth.laplace3d(128) if which == "laplace3d_128" else synth.powerlaw_random(1_000_000, 16.0, 2048, seed=0)
     M = gse.GseMatrix.from_csr(A, attach=(64, 32))
+    M.autotune(1)                  # the schedule the benchmark runs
     x = synth.uniform_x(A.n_cols, seed=0)
     xd = torch.from_numpy(x).cuda()
     rng = np.random.default_rng(1)
