@@ -179,14 +179,33 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gse")
-    ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--no-solve", action="store_true", help="skip every solver section")
+    ap.add_argument("--no-gmres", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--batch-systems", type=int, default=512)
+    ap.add_argument("--profile-spmv", nargs=2, metavar=("MATRIX", "K"), default=None,
+                    help="no timing: encode MATRIX (laplace3d_128 | powerlaw_1m), run gse_spmv at level K "
+                         "(1, 2, 3, 64 = FP64 CSR) three times and exit; the target for ncu captures")
+    ap.add_argument("--serve-requests", type=int, default=1000)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
         return
     import torch
     import paper_2411_04686_gb300 as gse
+    if args.profile_spmv:
+        name, k = args.profile_spmv[0], int(args.profile_spmv[1])
+        A = dict(build_workload())[name]
+        M = gse.GseMatrix.from_csr(A, attach=(64, 32))      # schedule from row statistics
+        x = torch.from_numpy(synth.uniform_x(A.n_cols, seed=0)).cuda()
+        y = torch.empty(A.n_rows, dtype=torch.float64, device="cuda")
+        for _ in range(3):
+            M.spmv(k, x, y)
+        torch.cuda.synchronize()
+        print(json.dumps({"profiled": name, "k": k, "schedule": M.info().schedule, "nnz": A.nnz}))
+        return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -202,12 +221,18 @@ def main():
     mats = build_workload()
     handles = []
     for name, A in mats:
-        M = gse.GseMatrix.from_csr(A, attach=(64, 32))
-        M.autotune(1)
+        M = gse.GseMatrix.from_csr(A, attach=(64, 32))      # schedule from row statistics
         x = torch.from_numpy(synth.uniform_x(A.n_cols, seed=0)).cuda()
         y = torch.empty(A.n_rows, dtype=torch.float64, device="cuda")
         handles.append((name, A, M, x, y))
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    flush_sink = torch.empty(1, dtype=torch.float32, device="cuda")
+
+    def flush_l2(v):
+        # write a buffer larger than L2, then read it back so that the dirty
+        # lines are written out before the timed kernel starts
+        flush.fill_(float(v))
+        flush_sink.copy_(flush.sum())
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(6)]
     launches = [(hi, k) for hi in range(len(handles)) for k in (1, 2, 3)]
 
@@ -215,7 +240,7 @@ def main():
         times = []
         for li, (hi, k) in enumerate(launches):
             name, A, M, x, y = handles[hi]
-            flush.fill_(float(li))
+            flush_l2(li)
             e0, e1 = ev[li]
             e0.record(stream)
             M.spmv(k, x, y)
@@ -287,7 +312,7 @@ def main():
         for lv, vb in ((gse.LEVEL_FP64, 8), (gse.LEVEL_FP32, 4)):
             ts = []
             for _ in range(10):
-                flush.fill_(1.0)
+                flush_l2(1)
                 e0, e1 = ev[0]
                 e0.record(stream)
                 M.spmv(lv, x, y)
@@ -320,9 +345,16 @@ def main():
     e2e = {"value": round(bytes_step * world / e2e_s / 1e9, 2), "unit": "GB/s",
            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
-    solve = None
+    solve = gmres = batched = served = None
     if not args.no_solve:
         solve = solver_comparison(gse, torch)
+        if not args.no_gmres:
+            gmres = gmres_comparison(gse, torch)
+        if not args.no_batch:
+            batched = batched_comparison(gse, torch, args.batch_systems, rank, world)
+        if not args.no_serve:
+            rate = 0.5 * batched["gse_stepped_batched"]["solves_per_s"] if batched else 200.0
+            served = served_benchmark(gse, torch, args.serve_requests, rate, rank, world)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -335,10 +367,11 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded; stand-ins for the paper's SuiteSparse sets)",
             "config": {"workload": "gse_spmv_sweep_laplace3d128_powerlaw1m", "levels": [1, 2, 3],
-                       "group_size": 32, "seg_bits": [16, 16, 20], "l2": "flushed (256 MiB write) before each SpMV",
+                       "group_size": 32, "seg_bits": [16, 16, 20], "l2": "flushed before each SpMV (256 MiB write, then a 256 MiB read so no dirty line is written back inside the timed kernel)",
                        "parallelism": "replicas" if world > 1 else "single_gpu",
                        "wall_s_timed_region": round(wall, 3)},
-            "roofline": roofline, "per_k": per_k, "baselines": baselines, "solve": solve,
+            "roofline": roofline, "per_k": per_k, "baselines": baselines, "solve": solve, "gmres": gmres,
+            "batched": batched, "served": served,
             "e2e": e2e, "gpu_launches": len(launches) * args.steps, "clocks": clocks,
             "cpu_baseline": cpu,
         }
@@ -376,6 +409,130 @@ def solver_comparison(gse, torch):
         out[name]["speedup_vs_fp64"] = round(f / out[name]["seconds"], 3)
     M.free()
     return out
+
+
+def gmres_comparison(gse, torch):
+    """Stepped GSE-GMRES(30) vs FP64 CSR GMRES(30) on the 2D convection-diffusion
+    operator 1024^2 (Peclet 10, upwind), tol 1e-10, at most 15000 iterations."""
+    A = synth.convdiff2d(1024, 10.0)
+    M = gse.GseMatrix.from_csr(A, attach=(64,))
+    b = torch.from_numpy(synth.rhs_ones(A)).cuda()
+    out = {"workload": "convdiff2d_1024_pe10_gmres30_tol1e-10", "n": A.n_rows, "nnz": A.nnz, "max_iter": 15000}
+    pol = gse.Policy(**{**gse.SCALED_GMRES.__dict__, "max_iter": 15000})
+    for name, p in (("fp64_csr_gmres", gse.fp64_policy(pol)), ("gse_stepped_gmres_paper_policy", pol)):
+        x = torch.zeros(A.n_rows, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info = M.gmres(b, x, tol=1e-10, policy=p)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        out[name] = {"seconds": round(dt, 4), "iters": info["iters"], "status": info["status"],
+                     "k_final": info["k_final"], "switch_iter": info["switch_iter"],
+                     "rel_res_true": info["rel_res_true"],
+                     "max_abs_err_vs_ones": float((x - 1.0).abs().max().item())}
+    out["gse_stepped_gmres_paper_policy"]["speedup_vs_fp64"] = round(
+        out["fp64_csr_gmres"]["seconds"] / out["gse_stepped_gmres_paper_policy"]["seconds"], 3)
+    M.free()
+    return out
+
+
+def batched_comparison(gse, torch, nsys, rank, world):
+    """nsys SPD systems of uneven size (n log-uniform 1e3..2.56e5, 2D/3D
+    anisotropic Laplacians with a diagonal shift) solved to 1e-10 in one
+    continuous batch; FP64 CSR in the same batched engine, and FP64 CSR CG one
+    system at a time (a sample of 32 systems, scaled)."""
+    specs = synth.shard_specs(synth.batch_specs(nsys, seed=0), rank, world) if world > 1 else synth.batch_specs(nsys, seed=0)
+    t0 = time.perf_counter()
+    As = [sp.build() for sp in specs]
+    t_gen = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    mats = [gse.GseMatrix.from_csr(A, attach=(64,)) for A in As]
+    torch.cuda.synchronize()
+    t_enc = time.perf_counter() - t0
+    bs = [torch.from_numpy(synth.rhs_ones(A)).cuda() for A in As]
+    out = {"workload": f"{len(As)} SPD Laplacians, n log-uniform 1e3..2.56e5, tol 1e-10",
+           "systems": len(As), "total_rows": int(sum(A.n_rows for A in As)),
+           "total_nnz": int(sum(A.nnz for A in As)), "host_generate_s": round(t_gen, 2),
+           "encode_s": round(t_enc, 3)}
+    for name, pol in (("gse_stepped_batched", gse.SCALED_CG), ("fp64_csr_batched", gse.fp64_policy(gse.SCALED_CG))):
+        xs = [torch.zeros(A.n_rows, dtype=torch.float64, device="cuda") for A in As]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, infos = gse.batch_cg(mats, bs, xs, tol=1e-10, policy=pol)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        out[name] = {"seconds": round(dt, 4), "solves_per_s": round(len(As) / dt, 2), "status": rc,
+                     "all_converged": all(i["status"] == gse.OK for i in infos),
+                     "max_iters": max(i["iters"] for i in infos),
+                     "max_rel_res_true": max(i["rel_res_true"] for i in infos)}
+    idx = list(range(0, len(As), max(1, len(As) // 32)))[:32]
+    t_single = 0.0
+    for i in idx:
+        x = torch.zeros(As[i].n_rows, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mats[i].cg(bs[i], x, tol=1e-10, policy=gse.fp64_policy(gse.SCALED_CG))
+        torch.cuda.synchronize()
+        t_single += time.perf_counter() - t0
+    est = t_single / len(idx) * len(As)
+    out["fp64_csr_one_at_a_time"] = {"seconds_estimated": round(est, 3), "sampled_systems": len(idx),
+                                     "solves_per_s": round(len(As) / est, 2)}
+    out["speedup_batched_gse_vs_one_at_a_time_fp64"] = round(est / out["gse_stepped_batched"]["seconds"], 2)
+    for M in mats:
+        M.free()
+    return out
+
+
+def served_benchmark(gse, torch, nreq, rate, rank, world):
+    """Poisson arrivals of nreq solve requests drawn from the batched
+    distribution (a pool of 64 systems), admitted by HBM footprint into a
+    continuous batch; p50/p99 latency from arrival to completion."""
+    from paper_2411_04686_gb300 import serve
+    specs = synth.batch_specs(64, seed=1)
+    pool = []
+    for sp in specs:
+        A = sp.build()
+        pool.append((A, synth.rhs_ones(A)))
+    arrivals = serve.poisson_arrivals(nreq, rate, seed=2)
+    rng = np.random.default_rng(3)
+    picks = rng.integers(0, len(pool), nreq)
+    reqs = [serve.Request(i, float(arrivals[i]), pool[picks[i]][0].n_rows, pool[picks[i]][0].nnz, int(picks[i]))
+            for i in range(nreq)]
+    if world > 1:
+        reqs = serve.shard(reqs, rank, world)
+    srv = serve.Server(lambda i: pool[i], capacity=64, slots_per_step=16)
+    t0 = time.perf_counter()
+    srv.clock = lambda: time.perf_counter() - t0
+    k = 0
+    while k < len(reqs) or srv.queue or srv.active:
+        now = srv.clock()
+        while k < len(reqs) and reqs[k].arrival <= now:
+            srv.submit(reqs[k])
+            k += 1
+        if not srv.queue and not srv.active and k < len(reqs):
+            time.sleep(max(0.0, min(0.01, reqs[k].arrival - now)))
+            continue
+        srv.step()
+    wall = srv.clock()
+    srv.close()
+    st = serve.latency_stats(srv.done)
+    ok = all(c.info["status"] == gse.OK for c in srv.done)
+    # one-at-a-time FP64 CSR CG throughput on the same pool (8 systems)
+    t_single = 0.0
+    for A, b in pool[:8]:
+        M = gse.GseMatrix.from_csr(A, attach=(64,))
+        bd = torch.from_numpy(b).cuda()
+        x = torch.zeros(A.n_rows, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        M.cg(bd, x, tol=1e-10, policy=gse.fp64_policy(gse.SCALED_CG))
+        torch.cuda.synchronize()
+        t_single += time.perf_counter() - t1
+        M.free()
+    return {"requests": len(reqs), "arrival_rate_per_s": round(rate, 2), "wall_s": round(wall, 3),
+            "solves_per_s": round(len(srv.done) / wall, 2), "p50_latency_s": round(st.get("p50_s", 0), 4),
+            "p99_latency_s": round(st.get("p99_s", 0), 4), "all_converged": ok,
+            "fp64_one_at_a_time_solves_per_s": round(8 / t_single, 2)}
 
 
 if __name__ == "__main__":

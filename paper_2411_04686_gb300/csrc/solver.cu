@@ -58,16 +58,16 @@ __device__ __forceinline__ bool sys_grid_sum(double v, double* partial, unsigned
 }
 
 // ITER: q = A p with the p.q epilogue; RESID: y = b - A x, no dot.  The engine
-// always runs one unit of 8 nonzeros per lane (chunks of 256).
+// runs one unit of 8 nonzeros per lane (chunks of 256), ENG_WARPS chunks per stage.
 template <bool ITER>
-__device__ __forceinline__ double eng_pipe(int k, const MatView& m, const double* x, const Epi& e, int64_t c0,
-                                           int64_t cs, int64_t nch, unsigned char* wsm, int* err) {
+__device__ __forceinline__ double eng_pipe(int k, const MatView& m, const double* x, const Epi& e, int64_t sc0,
+                                           int64_t scs, int64_t nch, unsigned char* smem, int* err) {
     switch (k) {
-        case 1: return spmv_warp_pipe<1, 0, 1, ITER, !ITER, ENG_STAGES>(m, x, e, c0, cs, nch, wsm, err);
-        case 2: return spmv_warp_pipe<2, 0, 1, ITER, !ITER, ENG_STAGES>(m, x, e, c0, cs, nch, wsm, err);
-        case 3: return spmv_warp_pipe<3, -1, 1, ITER, !ITER, ENG_STAGES>(m, x, e, c0, cs, nch, wsm, err);
-        case SRC_FP32: return spmv_warp_pipe<SRC_FP32, 0, 1, ITER, !ITER, ENG_STAGES>(m, x, e, c0, cs, nch, wsm, err);
-        default: return spmv_warp_pipe<SRC_FP64, 0, 1, ITER, !ITER, ENG_STAGES>(m, x, e, c0, cs, nch, wsm, err);
+        case 1: return spmv_chunks_block<1, 0, 1, ITER, !ITER, ENG_STAGES>(m, x, e, sc0, scs, nch, chunk_stage_layout<1, 0, 1>(ENG_WARPS, m.r_lo), smem, err);
+        case 2: return spmv_chunks_block<2, 0, 1, ITER, !ITER, ENG_STAGES>(m, x, e, sc0, scs, nch, chunk_stage_layout<2, 0, 1>(ENG_WARPS, m.r_lo), smem, err);
+        case 3: return spmv_chunks_block<3, -1, 1, ITER, !ITER, ENG_STAGES>(m, x, e, sc0, scs, nch, chunk_stage_layout<3, -1, 1>(ENG_WARPS, m.r_lo), smem, err);
+        case SRC_FP32: return spmv_chunks_block<SRC_FP32, 0, 1, ITER, !ITER, ENG_STAGES>(m, x, e, sc0, scs, nch, chunk_stage_layout<SRC_FP32, 0, 1>(ENG_WARPS, m.r_lo), smem, err);
+        default: return spmv_chunks_block<SRC_FP64, 0, 1, ITER, !ITER, ENG_STAGES>(m, x, e, sc0, scs, nch, chunk_stage_layout<SRC_FP64, 0, 1>(ENG_WARPS, m.r_lo), smem, err);
     }
 }
 
@@ -106,20 +106,18 @@ __global__ void __launch_bounds__(ENG_WARPS * 32) k_cg_p1(const SysDesc* __restr
     } else {
         e.kind = EPI_RESID; e.y = S.q; e.b = S.b; e.p = nullptr; x = S.x; k = S.prm.kmax;
     }
-    const int warp = threadIdx.x >> 5;
-    unsigned char* wsm = smem + warp * warp_smem;
-    const int64_t c0 = (int64_t)lb * ENG_WARPS + warp, cs = (int64_t)nblk * ENG_WARPS;
+    (void)warp_smem;
     const bool rows = S.sched == GSE_SCHEDULE_ROWS;
     const int64_t nsb = (S.n + 32 * ENG_WARPS - 1) / (32 * ENG_WARPS);
     if (!rows) fill_empty_rows(m, e, (int64_t)lb * blockDim.x + threadIdx.x, (int64_t)nblk * blockDim.x);
     if (mode == MODE_ITER) {
         const double dot = rows ? eng_rows<true>(k, m, x, e, lb, nblk, nsb, S.row_span, smem, S.err)
-                                : eng_pipe<true>(k, m, x, e, c0, cs, S.n_chunks, wsm, S.err);
+                                : eng_pipe<true>(k, m, x, e, lb, nblk, S.n_chunks, smem, S.err);
         double total;
         if (sys_grid_sum(dot, S.partial, S.counter, lb, nblk, red, &total) && threadIdx.x == 0) st->pq = total;
     } else {
         if (rows) eng_rows<false>(k, m, x, e, lb, nblk, nsb, S.row_span, smem, S.err);
-        else eng_pipe<false>(k, m, x, e, c0, cs, S.n_chunks, wsm, S.err);
+        else eng_pipe<false>(k, m, x, e, lb, nblk, S.n_chunks, smem, S.err);
     }
 }
 
@@ -782,7 +780,11 @@ extern "C" int gse_engine_poll(gse_engine e, int* done_slots, gse_solve_info* in
         if (!sl.active || e->h_state[i].mode != MODE_DONE) continue;
         gse_solve_info info;
         memset(&info, 0, sizeof(info));
-        fill_info(e, i, &info, true_residual(e, i));
+        // a converged system's true residual was computed on the device when it
+        // passed the check (x has not changed since); otherwise recompute it
+        const CgState& st = e->h_state[i];
+        const double tr = st.status == GSE_OK ? st.true_res : true_residual(e, i);
+        fill_info(e, i, &info, tr);
         if (done_slots) done_slots[c] = i;
         if (infos) infos[c] = info;
         sl.active = false;

@@ -68,10 +68,14 @@ __global__ void k_cg_fix(const SysDesc* __restrict__ sys, const int2* __restrict
 __global__ void k_cg_p2(const SysDesc* __restrict__ sys, const int2* __restrict__ map);
 __global__ void k_cg_p3(const SysDesc* __restrict__ sys, const int2* __restrict__ map);
 
-// Per-warp shared memory of P1: the largest stage layout over the value sources.
-constexpr int ENG_WARP_SMEM = warp_smem_bytes<SRC_FP64, 0, 1, ENG_STAGES>() > warp_smem_bytes<3, -1, 1, ENG_STAGES>()
-                                  ? warp_smem_bytes<SRC_FP64, 0, 1, ENG_STAGES>()
-                                  : warp_smem_bytes<3, -1, 1, ENG_STAGES>();
+// Per-warp share of P1's shared memory on the nonzero split: the CTA's stage
+// ring for the largest value source, divided over its warps.
+inline int eng_chunks_warp_smem() {
+    const int a = chunks_block_smem<ENG_STAGES, 1>(chunk_stage_layout<SRC_FP64, 0, 1>(ENG_WARPS, 16));
+    const int b = chunks_block_smem<ENG_STAGES, 1>(chunk_stage_layout<3, -1, 1>(ENG_WARPS, 16));
+    return ((a > b ? a : b) + ENG_WARPS - 1) / ENG_WARPS;
+}
+#define ENG_WARP_SMEM (eng_chunks_warp_smem())
 inline size_t p1_smem() { return (size_t)ENG_WARPS * ENG_WARP_SMEM; }
 
 // Largest per-warp shared memory P1 can need (row schedule at the widest span).
@@ -107,7 +111,7 @@ inline void sys_partition(SysDesc& d, const gse_matrix* h, int num_sms, int p1_r
         nbs = (d.n + 32 * ENG_WARPS - 1) / (32 * ENG_WARPS);
         if (nbs > (int64_t)num_sms * 4) nbs = (int64_t)num_sms * 4;   // fixed cap: independent of the batch
     } else {
-        nbs = (d.n_chunks + ENG_WARPS - 1) / ENG_WARPS;
+        nbs = (d.n_chunks + ENG_WARPS - 1) / ENG_WARPS;                // super-chunks
         if (nbs > (int64_t)num_sms * p1_resident) nbs = (int64_t)num_sms * p1_resident;
     }
     if (nbs < 1) nbs = 1;

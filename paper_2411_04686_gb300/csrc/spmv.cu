@@ -8,23 +8,21 @@
 
 namespace gse {
 
-constexpr int SPMV_WARPS = 4;
 constexpr int SPMV_STAGES = 3;
+// warps per CTA on the nonzero split: 8 / UPL, so a stage always holds 2048 nonzeros
+template <int UPL>
+constexpr int spmv_warps() { return 8 / UPL; }
 
-template <int K, int R, int UPL>
-constexpr size_t spmv_smem() { return (size_t)SPMV_WARPS * warp_smem_bytes<K, R, UPL, SPMV_STAGES>(); }
-
-// y = A_k x (or b - A_k x): every warp runs spmv_warp_pipe over its chunks.
+// y = A_k x (or b - A_k x) on the nonzero split: CTAs of 8/UPL warps walk
+// super-chunks of that many chunks through a TMA-filled stage ring.
 template <int K, int R, int UPL, bool RESID>
-__global__ void __launch_bounds__(SPMV_WARPS * 32) k_spmv(MatView m, const double* __restrict__ x, Epi e,
-                                                           int64_t n_chunks, int* err, const int* gate) {
+__global__ void __launch_bounds__(spmv_warps<UPL>() * 32) k_spmv(MatView m, const double* __restrict__ x, Epi e,
+                                                                  int64_t n_chunks, ChunkStage L, int* err,
+                                                                  const int* gate) {
     if (gate && *gate) return;
     extern __shared__ __align__(128) unsigned char smem[];
-    const int warp = threadIdx.x >> 5;
     fill_empty_rows(m, e, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
-    spmv_warp_pipe<K, R, UPL, false, RESID, SPMV_STAGES>(
-        m, x, e, (int64_t)blockIdx.x * SPMV_WARPS + warp, (int64_t)gridDim.x * SPMV_WARPS, n_chunks,
-        smem + warp * warp_smem_bytes<K, R, UPL, SPMV_STAGES>(), err);
+    spmv_chunks_block<K, R, UPL, false, RESID, SPMV_STAGES>(m, x, e, blockIdx.x, gridDim.x, n_chunks, L, smem, err);
 }
 
 // Finishes the rows that cross chunk boundaries (after k_spmv, same stream).
@@ -86,36 +84,48 @@ static int launch_rows(gse_matrix* h, int k, int epi, const SpmvArgs& a, cudaStr
     return cudaGetLastError() == cudaSuccess ? GSE_OK : GSE_ERR_CUDA;
 }
 
-typedef void (*SpmvKernel)(MatView, const double*, Epi, int64_t, int*, const int*);
+typedef void (*SpmvKernel)(MatView, const double*, Epi, int64_t, ChunkStage, int*, const int*);
 
 struct KernelPick {
     SpmvKernel fn;
+    ChunkStage L;
     size_t smem;
+    int warps;
 };
 
+template <int K, int R, int UPL, bool RESID>
+KernelPick pick_one(int r_lo) {
+    KernelPick kp;
+    kp.fn = k_spmv<K, R, UPL, RESID>;
+    kp.warps = spmv_warps<UPL>();
+    kp.L = chunk_stage_layout<K, R, UPL>(kp.warps, r_lo);
+    kp.smem = (size_t)chunks_block_smem<SPMV_STAGES, UPL>(kp.L);
+    return kp;
+}
+
 template <int K, int R, bool RESID>
-KernelPick pick_upl(int upl) {
+KernelPick pick_upl(int upl, int r_lo) {
     switch (upl) {
-        case 1: return {k_spmv<K, R, 1, RESID>, spmv_smem<K, R, 1>()};
-        case 2: return {k_spmv<K, R, 2, RESID>, spmv_smem<K, R, 2>()};
-        default: return {k_spmv<K, R, 4, RESID>, spmv_smem<K, R, 4>()};
+        case 1: return pick_one<K, R, 1, RESID>(r_lo);
+        case 2: return pick_one<K, R, 2, RESID>(r_lo);
+        default: return pick_one<K, R, 4, RESID>(r_lo);
     }
 }
 
 template <bool RESID>
 static KernelPick pick_kernel_t(int k, int r_lo, int upl) {
     switch (k) {
-        case 1: return pick_upl<1, 0, RESID>(upl);
-        case 2: return pick_upl<2, 0, RESID>(upl);
+        case 1: return pick_upl<1, 0, RESID>(upl, r_lo);
+        case 2: return pick_upl<2, 0, RESID>(upl, r_lo);
         case 3:
             switch (r_lo) {
-                case 0: return pick_upl<3, 0, RESID>(upl);
-                case 4: return pick_upl<3, 4, RESID>(upl);
-                case 8: return pick_upl<3, 8, RESID>(upl);
-                default: return pick_upl<3, 16, RESID>(upl);
+                case 0: return pick_upl<3, 0, RESID>(upl, r_lo);
+                case 4: return pick_upl<3, 4, RESID>(upl, r_lo);
+                case 8: return pick_upl<3, 8, RESID>(upl, r_lo);
+                default: return pick_upl<3, 16, RESID>(upl, r_lo);
             }
-        case SRC_FP32: return pick_upl<SRC_FP32, 0, RESID>(upl);
-        default: return pick_upl<SRC_FP64, 0, RESID>(upl);
+        case SRC_FP32: return pick_upl<SRC_FP32, 0, RESID>(upl, r_lo);
+        default: return pick_upl<SRC_FP64, 0, RESID>(upl, r_lo);
     }
 }
 
@@ -136,7 +146,7 @@ static int resident_blocks(const KernelPick& kp) {
         cudaFuncSetAttribute((const void*)kp.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kp.smem);
     cudaFuncSetAttribute((const void*)kp.fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kp.fn, SPMV_WARPS * 32, kp.smem) != cudaSuccess || nb < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kp.fn, kp.warps * 32, kp.smem) != cudaSuccess || nb < 1)
         nb = 1;
     if (nkeys < 128) {
         keys[nkeys] = (const void*)kp.fn;
@@ -153,9 +163,9 @@ int launch_spmv(gse_matrix* h, int k, int epi, const SpmvArgs& a, cudaStream_t s
     const int64_t ch = 256 * upl;
     const int64_t n_chunks = (h->v.nnz + ch - 1) / ch;
     const int64_t resident = (int64_t)h->num_sms * resident_blocks(kp);
-    int64_t g = (n_chunks + SPMV_WARPS - 1) / SPMV_WARPS;
+    int64_t g = (n_chunks + kp.warps - 1) / kp.warps;          // super-chunks
     if (g > resident) g = resident;
-    const int64_t gmin = (h->v.n_empty + SPMV_WARPS * 32 - 1) / (SPMV_WARPS * 32);
+    const int64_t gmin = (h->v.n_empty + kp.warps * 32 - 1) / (kp.warps * 32);
     if (g < gmin) g = gmin < resident ? gmin : resident;
     if (g < 1) g = 1;
     Epi e;
@@ -163,7 +173,7 @@ int launch_spmv(gse_matrix* h, int k, int epi, const SpmvArgs& a, cudaStream_t s
     e.y = a.y;
     e.b = a.b;
     e.p = a.p;
-    kp.fn<<<(unsigned)g, SPMV_WARPS * 32, kp.smem, s>>>(h->v, a.x, e, n_chunks, h->d_err, a.skip_flag);
+    kp.fn<<<(unsigned)g, kp.warps * 32, kp.smem, s>>>(h->v, a.x, e, n_chunks, kp.L, h->d_err, a.skip_flag);
     if (n_chunks > 1) {
         int64_t gf = (n_chunks + 255) / 256;
         if (gf > (int64_t)h->num_sms * 8) gf = (int64_t)h->num_sms * 8;

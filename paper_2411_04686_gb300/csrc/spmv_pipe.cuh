@@ -1,17 +1,17 @@
 // spmv_pipe.cuh -- the GSE-SpMV main loop with TMA-staged chunks.
 //
-// Each warp walks its chunks (c0, c0 + stride, ...) through a ring of STAGES
-// shared-memory stages.  Lane 0 fills a stage with 1-D bulk copies
-// (cp.async.bulk, completion counted in bytes on an mbarrier): the chunk's
-// column indices, its live segment arrays (or the CSR values of a baseline),
-// its row-end bits and its group exponents -- all contiguous, 16-byte aligned
-// slices of the HBM arrays.  While the warp computes chunk i, the copies for
-// chunks i+1 .. i+STAGES-1 are in flight and the x gathers of chunk i+1 have
-// already been issued (one chunk of look-ahead, in registers), so neither HBM
-// latency nor the gather latency sits on the FMA path.
+// Both schedules stage the matrix through a ring of shared-memory stages per
+// CTA.  One producer thread fills a stage with a few large 1-D bulk copies
+// (cp.async.bulk, completion counted in bytes on a "full" mbarrier): column
+// indices, the live segment arrays (or the CSR values of a baseline), row-end
+// bits and group exponents -- contiguous, 16-byte aligned slices of the HBM
+// arrays.  Every warp consumes its part, then arrives on the stage's "empty"
+// barrier; the producer refills the stage once all warps have left it.  Large
+// copies from one issuer per CTA keep the DRAM stream dense (on this GPU, many
+// small per-warp copies reach only 2-3 TB/s).
 //
-// Every mbarrier wait is bounded; on expiry the warp records GSE_TIMEOUT in
-// *err, waits (bounded again) for its own copies still in flight and returns.
+// Every mbarrier wait is bounded; on expiry the kernel records GSE_TIMEOUT in
+// *err and leaves the loop.
 #pragma once
 
 #include "spmv_core.cuh"
@@ -59,123 +59,6 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
         : "memory");
 }
 
-// Byte layout of one stage for value source K (GSE level or baseline).
-template <int K, int R, int UPL>
-struct StageLayout {
-    static constexpr int CH = 256 * UPL;
-    static constexpr int RMAX = R < 0 ? 16 : R;
-    static constexpr int OFF_COL = 0;
-    static constexpr int OFF_V = CH * 4;
-    static constexpr int SZ_V = K == SRC_FP64 ? CH * 8
-                              : K == SRC_FP32 ? CH * 4
-                              : CH * 2 * (K >= 3 ? 3 : K) + (K >= 3 ? CH * RMAX / 8 : 0);
-    static constexpr int OFF_RE = OFF_V + SZ_V;
-    static constexpr int OFF_GX = OFF_RE + CH / 8;
-    static constexpr int BYTES = ((OFF_GX + CH / 4) + 127) / 128 * 128;   // gexp: <= CH/8 entries of 2 B
-};
-
-// Lane 0: fills `stage` with chunk c and arms the barrier with the byte count.
-template <int K, int R, int UPL>
-__device__ __forceinline__ void issue_chunk(const MatView& m, int64_t c, unsigned char* stage, uint32_t bar) {
-    using L = StageLayout<K, R, UPL>;
-    constexpr int CH = L::CH;
-    const int64_t e0 = c * CH;
-    const uint32_t gx_bytes = (uint32_t)((CH >> m.g_shift) * 2);
-    uint32_t vbytes;
-    if constexpr (K == SRC_FP64) vbytes = CH * 8;
-    else if constexpr (K == SRC_FP32) vbytes = CH * 4;
-    else {
-        vbytes = CH * 2 * (K >= 3 ? 3 : K);
-        if constexpr (K >= 3) vbytes += (uint32_t)(CH * (R < 0 ? m.r_lo : R) / 8);
-    }
-    mbar_expect_tx(bar, (uint32_t)(CH * 4) + vbytes + CH / 8 + gx_bytes);
-    const uint32_t s = smem_u32(stage);
-    bulk_g2s(s + L::OFF_COL, m.col + e0, CH * 4, bar);
-    if constexpr (K == SRC_FP64) {
-        bulk_g2s(s + L::OFF_V, m.val64 + e0, CH * 8, bar);
-    } else if constexpr (K == SRC_FP32) {
-        bulk_g2s(s + L::OFF_V, m.val32 + e0, CH * 4, bar);
-    } else {
-        bulk_g2s(s + L::OFF_V, m.head + e0, CH * 2, bar);
-        if constexpr (K >= 2) bulk_g2s(s + L::OFF_V + CH * 2, m.tail1 + e0, CH * 2, bar);
-        if constexpr (K >= 3) {
-            bulk_g2s(s + L::OFF_V + CH * 4, m.t2hi + e0, CH * 2, bar);
-            const int r = R < 0 ? m.r_lo : R;
-            if (r > 0) bulk_g2s(s + L::OFF_V + CH * 6, m.t2lo + e0 / 8 * r / 4, (uint32_t)(CH * r / 8), bar);
-        }
-    }
-    bulk_g2s(s + L::OFF_RE, m.rowend + e0 / 32, CH / 8, bar);
-    bulk_g2s(s + L::OFF_GX, m.gexp + (e0 >> m.g_shift), gx_bytes, bar);
-}
-
-// Decodes the 8 values of the lane's unit ul (0 .. 32*UPL-1) from a stage.
-template <int K, int R, int UPL>
-__device__ __forceinline__ void unit_values(const MatView& m, const unsigned char* stage, int ul, double* a) {
-    using L = StageLayout<K, R, UPL>;
-    constexpr int CH = L::CH;
-    if constexpr (K == SRC_FP64) {
-        const double2* v2 = reinterpret_cast<const double2*>(stage + L::OFF_V) + 4 * ul;
-#pragma unroll
-        for (int j = 0; j < 4; j++) {
-            const double2 d = v2[j];
-            a[2 * j] = d.x;
-            a[2 * j + 1] = d.y;
-        }
-    } else if constexpr (K == SRC_FP32) {
-        const uint4* f4 = reinterpret_cast<const uint4*>(stage + L::OFF_V) + 2 * ul;
-        const uint4 fa = f4[0], fb = f4[1];
-        a[0] = widen_f32(fa.x); a[1] = widen_f32(fa.y); a[2] = widen_f32(fa.z); a[3] = widen_f32(fa.w);
-        a[4] = widen_f32(fb.x); a[5] = widen_f32(fb.y); a[6] = widen_f32(fb.z); a[7] = widen_f32(fb.w);
-    } else {
-        const uint16_t* gx = reinterpret_cast<const uint16_t*>(stage + L::OFF_GX);
-        const int Eg = gx[(ul * GSE_UNIT) >> m.g_shift];
-        const uint4 hw = reinterpret_cast<const uint4*>(stage + L::OFF_V)[ul];
-        uint4 t1w = make_uint4(0, 0, 0, 0), t2w = make_uint4(0, 0, 0, 0);
-        uint32_t lo[4] = {0, 0, 0, 0};
-        if constexpr (K >= 2) t1w = reinterpret_cast<const uint4*>(stage + L::OFF_V + CH * 2)[ul];
-        const int r = R < 0 ? m.r_lo : R;
-        if constexpr (K >= 3) {
-            t2w = reinterpret_cast<const uint4*>(stage + L::OFF_V + CH * 4)[ul];
-            const uint32_t* lw = reinterpret_cast<const uint32_t*>(stage + L::OFF_V + CH * 6);
-            if (r == 4) lo[0] = lw[ul];
-            else if (r == 8) { lo[0] = lw[2 * ul]; lo[1] = lw[2 * ul + 1]; }
-            else if (r == 16) { const uint4 l4 = reinterpret_cast<const uint4*>(lw)[ul]; lo[0] = l4.x; lo[1] = l4.y; lo[2] = l4.z; lo[3] = l4.w; }
-        }
-#pragma unroll
-        for (int i = 0; i < 8; i++) {
-            const uint32_t h = u16_of(hw, i);
-            if constexpr (K == 1) {
-                a[i] = decode_l1(h, Eg, m);
-            } else if constexpr (K == 2) {
-                a[i] = decode_l2(h, u16_of(t1w, i), Eg, m);
-            } else {
-                uint32_t t2 = u16_of(t2w, i);
-                if (r > 0) {
-                    const int bit = i * r;
-                    t2 = (t2 << r) | ((lo[bit >> 5] >> (bit & 31)) & ((1u << r) - 1u));
-                }
-                a[i] = decode_l3(h, u16_of(t1w, i), t2, Eg, m);
-            }
-        }
-    }
-}
-
-// Issues the lane's x gathers for the chunk in `stage`.
-template <int K, int R, int UPL>
-__device__ __forceinline__ void gather_x(const unsigned char* stage, const double* __restrict__ x, int lane,
-                                         double* xv) {
-    using L = StageLayout<K, R, UPL>;
-    const int4* c4 = reinterpret_cast<const int4*>(stage + L::OFF_COL) + 2 * UPL * lane;
-#pragma unroll
-    for (int q = 0; q < UPL; q++) {
-        const int4 ca = c4[2 * q], cb = c4[2 * q + 1];
-        xv[8 * q + 0] = __ldg(x + ca.x); xv[8 * q + 1] = __ldg(x + ca.y);
-        xv[8 * q + 2] = __ldg(x + ca.z); xv[8 * q + 3] = __ldg(x + ca.w);
-        xv[8 * q + 4] = __ldg(x + cb.x); xv[8 * q + 5] = __ldg(x + cb.y);
-        xv[8 * q + 6] = __ldg(x + cb.z); xv[8 * q + 7] = __ldg(x + cb.w);
-    }
-}
-
 struct ChunkScalars {
     int64_t row0;
     bool starts_mid;
@@ -190,183 +73,6 @@ __device__ __forceinline__ ChunkScalars chunk_scalars(const MatView& m, int64_t 
         s.starts_mid = !((__ldg(m.rowend + (pe >> 5)) >> (pe & 31)) & 1u);
     }
     return s;
-}
-
-// Row logic of one chunk: the FMAs with the gathered x, lane and warp stitching,
-// coalesced write-back through the epilogue, pieces of rows crossing chunks.
-template <int K, int R, int UPL, bool DOT, bool RESID>
-__device__ __forceinline__ double compute_chunk(const MatView& m, const Epi& e, int64_t c, const unsigned char* stage,
-                                                const double* xv, ChunkScalars sc, double* yb) {
-    using L = StageLayout<K, R, UPL>;
-    const unsigned FULL = 0xFFFFFFFFu;
-    const int lane = threadIdx.x & 31;
-    const uint32_t* re = reinterpret_cast<const uint32_t*>(stage + L::OFF_RE);
-    uint32_t bits;
-    if constexpr (UPL == 4) bits = re[lane];
-    else if constexpr (UPL == 2) bits = (re[lane >> 1] >> ((lane & 1) * 16)) & 0xFFFFu;
-    else bits = (re[lane >> 2] >> ((lane & 3) * 8)) & 0xFFu;
-    const int cnt = __popc(bits);
-    int incl = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(FULL, incl, o);
-        if (lane >= o) incl += t;
-    }
-    const int excl = incl - cnt;
-    const int total_ends = __shfl_sync(FULL, incl, 31);
-
-    double cur = 0.0, hp = 0.0;
-    int j = 0;
-#pragma unroll
-    for (int q = 0; q < UPL; q++) {
-        double a[8];
-        unit_values<K, R, UPL>(m, stage, lane * UPL + q, a);
-#pragma unroll
-        for (int i = 0; i < 8; i++) {
-            cur = fma(a[i], xv[8 * q + i], cur);
-            if ((bits >> (q * 8 + i)) & 1u) {
-                if (j == 0) hp = cur;
-                else yb[excl + j] = cur;
-                j++;
-                cur = 0.0;
-            }
-        }
-    }
-    const bool seen = j > 0;
-    const double co = cur;
-    double out;
-    if (__all_sync(FULL, seen)) {
-        out = co;
-    } else {
-        double v = co;
-        bool f = seen;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const double vu = __shfl_up_sync(FULL, v, o);
-            const bool fu = __shfl_up_sync(FULL, (int)f, o) != 0;
-            if (lane >= o) {
-                if (!f) v += vu;
-                f = f || fu;
-            }
-        }
-        out = v;
-    }
-    double in = __shfl_up_sync(FULL, out, 1);
-    if (lane == 0) in = 0.0;
-    if (seen) yb[excl] = in + hp;
-    const double out31 = __shfl_sync(FULL, out, 31);
-    const bool last_end = __shfl_sync(FULL, (bits >> (8 * UPL - 1)) & 1u, 31) != 0;
-    __syncwarp();
-    double dot = 0.0;
-    for (int idx = lane; idx < total_ends; idx += 32) {
-        if (idx == 0 && sc.starts_mid) continue;
-        const int64_t Rw = actual_row(m, sc.row0 + idx);
-        const double v = yb[idx];
-        if (DOT) dot = fma(__ldg(e.p + Rw), v, dot);
-        epi_finish_t<RESID>(e, Rw, v);
-    }
-    if (lane == 0) {
-        if (total_ends == 0) {
-            if (sc.row0 < m.n_nonempty) {
-                if (DOT) dot = fma(__ldg(e.p + actual_row(m, sc.row0)), out31, dot);
-                if (sc.starts_mid) m.part[c] = out31;
-                else m.carry[c] = out31;
-            }
-        } else {
-            if (sc.starts_mid) {
-                if (DOT) dot = fma(__ldg(e.p + actual_row(m, sc.row0)), yb[0], dot);
-                m.part[c] = yb[0];
-            }
-            const int64_t ro = sc.row0 + total_ends;
-            if (!last_end && ro < m.n_nonempty) {
-                if (DOT) dot = fma(__ldg(e.p + actual_row(m, ro)), out31, dot);
-                m.carry[c] = out31;
-            }
-        }
-    }
-    __syncwarp();
-    return dot;
-}
-
-// Shared memory one warp needs: barriers, STAGES stages, the row staging buffer.
-template <int K, int R, int UPL, int STAGES>
-__host__ __device__ constexpr int warp_smem_bytes() {
-    return 128 + STAGES * StageLayout<K, R, UPL>::BYTES + 256 * UPL * 8;
-}
-
-// The warp's whole share of an SpMV: chunks c0, c0 + cstride, ... < nch.
-// wsm: this warp's shared memory (warp_smem_bytes, 128-byte aligned).
-template <int K, int R, int UPL, bool DOT, bool RESID, int STAGES>
-__device__ __forceinline__ double spmv_warp_pipe(const MatView& m, const double* __restrict__ x, const Epi& e,
-                                                 int64_t c0, int64_t cstride, int64_t nch, unsigned char* wsm,
-                                                 int* err) {
-    using L = StageLayout<K, R, UPL>;
-    constexpr int CH = L::CH;
-    const int lane = threadIdx.x & 31;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(wsm);
-    unsigned char* stages = wsm + 128;
-    double* yb = reinterpret_cast<double*>(wsm + 128 + STAGES * L::BYTES);
-    double dot = 0.0;
-    if (c0 >= nch) return dot;
-    if (lane == 0) {
-        for (int s = 0; s < STAGES; s++) mbar_init(smem_u32(bars + s), 1);
-        fence_mbar_init();
-        for (int s = 0; s < STAGES; s++) {
-            const int64_t c = c0 + s * cstride;
-            if (c < nch) issue_chunk<K, R, UPL>(m, c, stages + s * L::BYTES, smem_u32(bars + s));
-        }
-    }
-    __syncwarp();
-    const unsigned FULL = 0xFFFFFFFFu;
-    uint32_t phases = 0, pending = 0;
-    for (int s = 0; s < STAGES; s++)
-        if (c0 + s * cstride < nch) pending |= 1u << s;
-    double xn[8 * UPL], xc[8 * UPL];
-    ChunkScalars sn, scur;
-    bool ok = __all_sync(FULL, mbar_wait_bounded(smem_u32(bars), 0));
-    if (ok) {
-        phases ^= 1u;
-        pending &= ~1u;
-        gather_x<K, R, UPL>(stages, x, lane, xn);
-        sn = chunk_scalars(m, c0, CH, UPL);
-    }
-    int64_t i = 0;
-    for (int64_t c = c0; ok && c < nch; c += cstride, i++) {
-        const int s = (int)(i % STAGES);
-#pragma unroll
-        for (int t = 0; t < 8 * UPL; t++) xc[t] = xn[t];
-        scur = sn;
-        const int64_t cn = c + cstride;
-        if (cn < nch) {
-            const int s1 = (int)((i + 1) % STAGES);
-            ok = __all_sync(FULL, mbar_wait_bounded(smem_u32(bars + s1), (phases >> s1) & 1u));
-            if (!ok) break;
-            phases ^= 1u << s1;
-            pending &= ~(1u << s1);
-            gather_x<K, R, UPL>(stages + s1 * L::BYTES, x, lane, xn);
-            sn = chunk_scalars(m, cn, CH, UPL);
-        }
-        dot += compute_chunk<K, R, UPL, DOT, RESID>(m, e, c, stages + s * L::BYTES, xc, scur, yb);
-        const int64_t ci = c + (int64_t)STAGES * cstride;
-        if (ci < nch) {
-            if (lane == 0) {
-                fence_proxy_async_smem();
-                issue_chunk<K, R, UPL>(m, ci, stages + s * L::BYTES, smem_u32(bars + s));
-            }
-            pending |= 1u << s;
-        }
-    }
-    if (!ok) {
-        // record the timeout, then give the copies already issued a bounded
-        // chance to land before the warp leaves
-        if (lane == 0) {
-            atomicOr(err, 1);
-            for (int s = 0; s < STAGES; s++)
-                if ((pending >> s) & 1u) mbar_wait_bounded(smem_u32(bars + s), (phases >> s) & 1u);
-        }
-        __syncwarp();
-    }
-    return dot;
 }
 
 }  // namespace gse
@@ -474,113 +180,6 @@ __device__ __forceinline__ double row_value(const MatView& m, const RowStage& L,
         return decode_l3(h, t1, t2, Eg, m);
     }
 }
-
-template <int K, int R, bool DOT, bool RESID, int STAGES>
-__device__ __forceinline__ double spmv_rows_pipe(const MatView& m, const double* __restrict__ x, const Epi& e,
-                                                 int64_t b0, int64_t bstride, int64_t nblocks, const RowStage& L,
-                                                 unsigned char* wsm, int* err) {
-    const unsigned FULL = 0xFFFFFFFFu;
-    const int lane = threadIdx.x & 31;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(wsm);
-    unsigned char* stages = wsm + 128;
-    double dot = 0.0;
-    if (b0 >= nblocks) return dot;
-    const int64_t n = m.n_rows;
-    // nonzero range of a block of 32 rows (same value in every lane)
-    auto block_bounds = [&](int64_t blk, int64_t* s0, int64_t* t0) {
-        const int64_t r0 = blk * 32, r1 = r0 + 32 < n ? r0 + 32 : n;
-        *s0 = __ldg(m.row_ptr + r0);
-        *t0 = __ldg(m.row_ptr + r1);
-    };
-    // the lane's own row
-    auto lane_row = [&](int64_t blk, int64_t* rs, int64_t* rt) {
-        const int64_t r = blk * 32 + lane;
-        *rs = __ldg(m.row_ptr + (r < n ? r : n));
-        *rt = __ldg(m.row_ptr + (r < n ? r + 1 : n));
-    };
-    if (lane == 0) {
-        for (int s = 0; s < STAGES; s++) mbar_init(smem_u32(bars + s), 1);
-        fence_mbar_init();
-    }
-    __syncwarp();
-    uint32_t phases = 0, pending = 0;
-    for (int s = 0; s < STAGES; s++) {
-        const int64_t blk = b0 + s * bstride;
-        if (blk >= nblocks) break;
-        int64_t bs, bt;
-        block_bounds(blk, &bs, &bt);
-        if (lane == 0) issue_rows<K, R>(m, L, row_block(bs, bt, m.g_shift), stages + s * L.bytes, smem_u32(bars + s));
-        pending |= 1u << s;
-    }
-    // bounds needed later are loaded one iteration ahead, so no global load
-    // sits between a wait and the next issue
-    int64_t rs_n, rt_n, cb_s, cb_t, is_n = 0, it_n = 0;
-    lane_row(b0, &rs_n, &rt_n);
-    block_bounds(b0, &cb_s, &cb_t);
-    if (b0 + (int64_t)STAGES * bstride < nblocks) block_bounds(b0 + (int64_t)STAGES * bstride, &is_n, &it_n);
-    bool ok = true;
-    int64_t i = 0;
-    for (int64_t blk = b0; blk < nblocks; blk += bstride, i++) {
-        const int s = (int)(i % STAGES);
-        const int64_t rs = rs_n, rt = rt_n;
-        const RowBlock rb = row_block(cb_s, cb_t, m.g_shift);
-        const int64_t nxt = blk + bstride, bi = blk + (int64_t)STAGES * bstride;
-        const int64_t is = is_n, it = it_n;
-        if (nxt < nblocks) {
-            lane_row(nxt, &rs_n, &rt_n);
-            block_bounds(nxt, &cb_s, &cb_t);
-        }
-        if (bi + bstride < nblocks) block_bounds(bi + bstride, &is_n, &it_n);
-        ok = __all_sync(FULL, mbar_wait_bounded(smem_u32(bars + s), (phases >> s) & 1u));
-        if (!ok) break;
-        phases ^= 1u << s;
-        pending &= ~(1u << s);
-        const unsigned char* st = stages + s * L.bytes;
-        // the lane's row with 32-bit stage-local indices; loads of 4 nonzeros
-        // are issued before their FMAs and no FMA is predicated off
-        double acc = 0.0;
-        const int32_t* scol = reinterpret_cast<const int32_t*>(st);
-        const int ls = (int)(rs - rb.e_lo), lt = (int)(rt - rb.e_lo);
-        const int goff = (int)((rb.e_lo >> m.g_shift) - rb.g_lo);
-        int li = ls;
-        for (; li + 4 <= lt; li += 4) {
-            double xv[4], av[4];
-#pragma unroll
-            for (int u = 0; u < 4; u++) xv[u] = __ldg(x + scol[li + u]);
-#pragma unroll
-            for (int u = 0; u < 4; u++) av[u] = row_value<K, R>(m, L, st, li + u, goff);
-#pragma unroll
-            for (int u = 0; u < 4; u++) acc = fma(av[u], xv[u], acc);
-        }
-        for (; li < lt; li++) acc = fma(row_value<K, R>(m, L, st, li, goff), __ldg(x + scol[li]), acc);
-        const int64_t r = blk * 32 + lane;
-        if (r < n) {
-            if (DOT) dot = fma(__ldg(e.p + r), acc, dot);
-            epi_finish_t<RESID>(e, r, acc);
-        }
-        __syncwarp();
-        if (bi < nblocks) {
-            if (lane == 0) {
-                fence_proxy_async_smem();
-                issue_rows<K, R>(m, L, row_block(is, it, m.g_shift), stages + s * L.bytes, smem_u32(bars + s));
-            }
-            pending |= 1u << s;
-        }
-    }
-    if (!ok) {
-        if (lane == 0) {
-            atomicOr(err, 1);
-            for (int s = 0; s < STAGES; s++)
-                if ((pending >> s) & 1u) mbar_wait_bounded(smem_u32(bars + s), (phases >> s) & 1u);
-        }
-        __syncwarp();
-    }
-    return dot;
-}
-
-// Shared memory of one warp on the row schedule.
-template <int STAGES>
-__host__ __device__ inline int rows_warp_smem(const RowStage& L) { return 128 + STAGES * L.bytes; }
 
 }  // namespace gse
 
@@ -704,5 +303,301 @@ __device__ __forceinline__ double spmv_rows_block(const MatView& m, const double
 // Shared memory of a CTA on the block-level row schedule.
 template <int STAGES>
 __host__ __device__ inline int rows_block_smem(const RowStage& L) { return 128 + STAGES * L.bytes; }
+
+}  // namespace gse
+
+namespace gse {
+
+// ---- nonzero-split schedule, block-level pipeline ---------------------------
+// A CTA of W warps owns super-chunks of W consecutive chunks (W * 256 * UPL
+// nonzeros); one producer thread stages a super-chunk with large bulk copies
+// and each warp runs the chunk logic (row-end bits, lane scans, split-row
+// pieces) on its own chunk c = super-chunk * W + warp.  Same chunk numbering as
+// the per-warp variant, so the split-row pass is unchanged.
+
+struct ChunkStage {
+    int nch;                        // chunks per stage (W)
+    int ch;                         // nonzeros per chunk
+    int off_v, off_re, off_gx, bytes;
+};
+
+template <int K, int R, int UPL>
+__host__ __device__ inline ChunkStage chunk_stage_layout(int W, int r_lo) {
+    ChunkStage L;
+    L.nch = W;
+    L.ch = 256 * UPL;
+    const int e = W * L.ch;
+    L.off_v = e * 4;
+    int v;
+    if (K == SRC_FP64) v = e * 8;
+    else if (K == SRC_FP32) v = e * 4;
+    else v = e * 2 * (K >= 3 ? 3 : K) + (K >= 3 ? e * (R < 0 ? r_lo : R) / 8 : 0);
+    L.off_re = L.off_v + ((v + 127) / 128) * 128;
+    L.off_gx = L.off_re + ((e / 8 + 127) / 128) * 128;
+    L.bytes = ((L.off_gx + e / 4) + 127) / 128 * 128;   // gexp: e / G * 2 <= e / 4 bytes
+    return L;
+}
+
+template <int K, int R, int UPL>
+__device__ __forceinline__ void issue_superchunk(const MatView& m, const ChunkStage& L, int64_t sc, int64_t nch_total,
+                                                 unsigned char* stage, uint32_t bar) {
+    // chunks sc*W .. min(sc*W + W, nch_total) - 1 (the tail super-chunk may be short)
+    int64_t c0 = sc * L.nch, c1 = c0 + L.nch < nch_total ? c0 + L.nch : nch_total;
+    const uint32_t e = (uint32_t)((c1 - c0) * L.ch);
+    const int64_t e0 = c0 * L.ch;
+    const int r = R < 0 ? m.r_lo : R;
+    const uint32_t gx_bytes = (uint32_t)((e >> m.g_shift) * 2);
+    uint32_t vbytes;
+    if constexpr (K == SRC_FP64) vbytes = e * 8;
+    else if constexpr (K == SRC_FP32) vbytes = e * 4;
+    else vbytes = e * 2 * (K >= 3 ? 3 : K) + (K >= 3 ? e * r / 8 : 0);
+    const bool gse_src = K != SRC_FP64 && K != SRC_FP32;
+    mbar_expect_tx(bar, e * 4 + vbytes + e / 8 + (gse_src ? gx_bytes : 0));
+    const uint32_t s = smem_u32(stage);
+    const uint32_t E = (uint32_t)(L.nch * L.ch);    // full-stage stride of the segment arrays
+    bulk_g2s(s, m.col + e0, e * 4, bar);
+    if constexpr (K == SRC_FP64) {
+        bulk_g2s(s + L.off_v, m.val64 + e0, e * 8, bar);
+    } else if constexpr (K == SRC_FP32) {
+        bulk_g2s(s + L.off_v, m.val32 + e0, e * 4, bar);
+    } else {
+        bulk_g2s(s + L.off_v, m.head + e0, e * 2, bar);
+        if constexpr (K >= 2) bulk_g2s(s + L.off_v + E * 2, m.tail1 + e0, e * 2, bar);
+        if constexpr (K >= 3) {
+            bulk_g2s(s + L.off_v + E * 4, m.t2hi + e0, e * 2, bar);
+            if (r > 0) bulk_g2s(s + L.off_v + E * 6, m.t2lo + e0 / 8 * r / 4, e * r / 8, bar);
+        }
+        bulk_g2s(s + L.off_gx, m.gexp + (e0 >> m.g_shift), gx_bytes, bar);
+    }
+    bulk_g2s(s + L.off_re, m.rowend + e0 / 32, e / 8, bar);
+}
+
+// Values of unit u (stage-relative unit index) of a block-level stage.
+template <int K, int R>
+__device__ __forceinline__ void unit_values_blk(const MatView& m, const ChunkStage& L, const unsigned char* stage,
+                                                int u, double* a) {
+    const int E = L.nch * L.ch;
+    if constexpr (K == SRC_FP64) {
+        const double2* v2 = reinterpret_cast<const double2*>(stage + L.off_v) + 4 * u;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const double2 d = v2[j];
+            a[2 * j] = d.x;
+            a[2 * j + 1] = d.y;
+        }
+    } else if constexpr (K == SRC_FP32) {
+        const uint4* f4 = reinterpret_cast<const uint4*>(stage + L.off_v) + 2 * u;
+        const uint4 fa = f4[0], fb = f4[1];
+        a[0] = widen_f32(fa.x); a[1] = widen_f32(fa.y); a[2] = widen_f32(fa.z); a[3] = widen_f32(fa.w);
+        a[4] = widen_f32(fb.x); a[5] = widen_f32(fb.y); a[6] = widen_f32(fb.z); a[7] = widen_f32(fb.w);
+    } else {
+        const uint16_t* gx = reinterpret_cast<const uint16_t*>(stage + L.off_gx);
+        const int Eg = gx[(u * GSE_UNIT) >> m.g_shift];
+        const uint4 hw = reinterpret_cast<const uint4*>(stage + L.off_v)[u];
+        uint4 t1w = make_uint4(0, 0, 0, 0), t2w = make_uint4(0, 0, 0, 0);
+        uint32_t lo[4] = {0, 0, 0, 0};
+        if constexpr (K >= 2) t1w = reinterpret_cast<const uint4*>(stage + L.off_v + E * 2)[u];
+        const int r = R < 0 ? m.r_lo : R;
+        if constexpr (K >= 3) {
+            t2w = reinterpret_cast<const uint4*>(stage + L.off_v + E * 4)[u];
+            const uint32_t* lw = reinterpret_cast<const uint32_t*>(stage + L.off_v + E * 6);
+            if (r == 4) lo[0] = lw[u];
+            else if (r == 8) { lo[0] = lw[2 * u]; lo[1] = lw[2 * u + 1]; }
+            else if (r == 16) { const uint4 l4 = reinterpret_cast<const uint4*>(lw)[u]; lo[0] = l4.x; lo[1] = l4.y; lo[2] = l4.z; lo[3] = l4.w; }
+        }
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            const uint32_t h = u16_of(hw, i);
+            if constexpr (K == 1) {
+                a[i] = decode_l1_f(h, Eg, (uint32_t)(Eg - m.W1 - 127) << 20, m);
+            } else if constexpr (K == 2) {
+                a[i] = decode_l2(h, u16_of(t1w, i), Eg, m);
+            } else {
+                uint32_t t2 = u16_of(t2w, i);
+                if (r > 0) {
+                    const int bit = i * r;
+                    t2 = (t2 << r) | ((lo[bit >> 5] >> (bit & 31)) & ((1u << r) - 1u));
+                }
+                a[i] = decode_l3(h, u16_of(t1w, i), t2, Eg, m);
+            }
+        }
+    }
+}
+
+// One warp's chunk c from a block-level stage (its units start at ub).
+template <int K, int R, int UPL, bool DOT, bool RESID>
+__device__ __forceinline__ double compute_chunk_blk(const MatView& m, const Epi& e, int64_t c, const ChunkStage& L,
+                                                    const unsigned char* stage, int ub, const double* __restrict__ x,
+                                                    ChunkScalars sc, double* yb) {
+    const unsigned FULL = 0xFFFFFFFFu;
+    const int lane = threadIdx.x & 31;
+    const uint32_t* re = reinterpret_cast<const uint32_t*>(stage + L.off_re) + (ub >> 2);
+    uint32_t bits;
+    if constexpr (UPL == 4) bits = re[lane];
+    else if constexpr (UPL == 2) bits = (re[lane >> 1] >> ((lane & 1) * 16)) & 0xFFFFu;
+    else bits = (re[lane >> 2] >> ((lane & 3) * 8)) & 0xFFu;
+    // x gathers for the lane's 8*UPL nonzeros, issued before the scans
+    double xv[8 * UPL];
+    const int4* c4 = reinterpret_cast<const int4*>(stage) + 2 * (ub + UPL * lane);
+#pragma unroll
+    for (int q = 0; q < UPL; q++) {
+        const int4 ca = c4[2 * q], cb = c4[2 * q + 1];
+        xv[8 * q + 0] = __ldg(x + ca.x); xv[8 * q + 1] = __ldg(x + ca.y);
+        xv[8 * q + 2] = __ldg(x + ca.z); xv[8 * q + 3] = __ldg(x + ca.w);
+        xv[8 * q + 4] = __ldg(x + cb.x); xv[8 * q + 5] = __ldg(x + cb.y);
+        xv[8 * q + 6] = __ldg(x + cb.z); xv[8 * q + 7] = __ldg(x + cb.w);
+    }
+    const int cnt = __popc(bits);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const int excl = incl - cnt;
+    const int total_ends = __shfl_sync(FULL, incl, 31);
+    double cur = 0.0, hp = 0.0;
+    int j = 0;
+#pragma unroll
+    for (int q = 0; q < UPL; q++) {
+        double a[8];
+        unit_values_blk<K, R>(m, L, stage, ub + lane * UPL + q, a);
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            cur = fma(a[i], xv[8 * q + i], cur);
+            if ((bits >> (q * 8 + i)) & 1u) {
+                if (j == 0) hp = cur;
+                else yb[excl + j] = cur;
+                j++;
+                cur = 0.0;
+            }
+        }
+    }
+    const bool seen = j > 0;
+    const double co = cur;
+    double out;
+    if (__all_sync(FULL, seen)) {
+        out = co;
+    } else {
+        double v = co;
+        bool f = seen;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const double vu = __shfl_up_sync(FULL, v, o);
+            const bool fu = __shfl_up_sync(FULL, (int)f, o) != 0;
+            if (lane >= o) {
+                if (!f) v += vu;
+                f = f || fu;
+            }
+        }
+        out = v;
+    }
+    double in = __shfl_up_sync(FULL, out, 1);
+    if (lane == 0) in = 0.0;
+    if (seen) yb[excl] = in + hp;
+    const double out31 = __shfl_sync(FULL, out, 31);
+    const bool last_end = __shfl_sync(FULL, (bits >> (8 * UPL - 1)) & 1u, 31) != 0;
+    __syncwarp();
+    double dot = 0.0;
+    for (int idx = lane; idx < total_ends; idx += 32) {
+        if (idx == 0 && sc.starts_mid) continue;
+        const int64_t Rw = actual_row(m, sc.row0 + idx);
+        const double v = yb[idx];
+        if (DOT) dot = fma(__ldg(e.p + Rw), v, dot);
+        epi_finish_t<RESID>(e, Rw, v);
+    }
+    if (lane == 0) {
+        if (total_ends == 0) {
+            if (sc.row0 < m.n_nonempty) {
+                if (DOT) dot = fma(__ldg(e.p + actual_row(m, sc.row0)), out31, dot);
+                if (sc.starts_mid) m.part[c] = out31;
+                else m.carry[c] = out31;
+            }
+        } else {
+            if (sc.starts_mid) {
+                if (DOT) dot = fma(__ldg(e.p + actual_row(m, sc.row0)), yb[0], dot);
+                m.part[c] = yb[0];
+            }
+            const int64_t ro = sc.row0 + total_ends;
+            if (!last_end && ro < m.n_nonempty) {
+                if (DOT) dot = fma(__ldg(e.p + actual_row(m, ro)), out31, dot);
+                m.carry[c] = out31;
+            }
+        }
+    }
+    __syncwarp();
+    return dot;
+}
+
+// The CTA's share of an SpMV on the nonzero split: super-chunks sc0, sc0 +
+// scstride, ... of W chunks each (nch_total chunks in all).  smem: STAGES
+// stages, then W row-staging buffers of 256*UPL doubles.
+template <int K, int R, int UPL, bool DOT, bool RESID, int STAGES>
+__device__ __forceinline__ double spmv_chunks_block(const MatView& m, const double* __restrict__ x, const Epi& e,
+                                                    int64_t sc0, int64_t scstride, int64_t nch_total,
+                                                    const ChunkStage& L, unsigned char* smem, int* err) {
+    const unsigned FULL = 0xFFFFFFFFu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = L.nch;
+    constexpr int CH = 256 * UPL;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem);
+    uint64_t* empty = full + STAGES;
+    unsigned char* stages = smem + 128;
+    double* yb = reinterpret_cast<double*>(smem + 128 + STAGES * L.bytes) + warp * CH;
+    const bool producer = threadIdx.x == 0;
+    const int64_t nsc = (nch_total + W - 1) / W;
+    double dot = 0.0;
+    if (sc0 >= nsc) return dot;
+    if (producer) {
+        for (int s = 0; s < STAGES; s++) {
+            mbar_init(smem_u32(full + s), 1);
+            mbar_init(smem_u32(empty + s), W);
+        }
+        fence_mbar_init();
+        for (int s = 0; s < STAGES; s++) {
+            const int64_t sc = sc0 + s * scstride;
+            if (sc >= nsc) break;
+            issue_superchunk<K, R, UPL>(m, L, sc, nch_total, stages + s * L.bytes, smem_u32(full + s));
+        }
+    }
+    __syncthreads();
+    uint32_t fphase = 0, ephase = 0;
+    bool ok = true;
+    int64_t i = 0;
+    ChunkScalars scn;
+    {
+        const int64_t c = sc0 * W + warp;
+        if (c < nch_total) scn = chunk_scalars(m, c, CH, UPL);
+    }
+    for (int64_t sc = sc0; sc < nsc; sc += scstride, i++) {
+        const int s = (int)(i % STAGES);
+        const int64_t c = sc * W + warp;
+        const ChunkScalars scs = scn;
+        const int64_t cn = (sc + scstride) * W + warp;
+        if (sc + scstride < nsc && cn < nch_total) scn = chunk_scalars(m, cn, CH, UPL);
+        ok = __all_sync(FULL, mbar_wait_bounded(smem_u32(full + s), (fphase >> s) & 1u));
+        if (!ok) break;
+        fphase ^= 1u << s;
+        if (c < nch_total)
+            dot += compute_chunk_blk<K, R, UPL, DOT, RESID>(m, e, c, L, stages + s * L.bytes, warp * 32 * UPL, x, scs, yb);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(empty + s));
+        const int64_t si = sc + (int64_t)STAGES * scstride;
+        if (producer && si < nsc) {
+            if (!mbar_wait_bounded(smem_u32(empty + s), (ephase >> s) & 1u)) atomicOr(err, 1);
+            else {
+                fence_proxy_async_smem();
+                issue_superchunk<K, R, UPL>(m, L, si, nch_total, stages + s * L.bytes, smem_u32(full + s));
+            }
+        }
+        ephase ^= 1u << s;
+    }
+    if (!ok && lane == 0) atomicOr(err, 1);
+    return dot;
+}
+
+template <int STAGES, int UPL>
+__host__ __device__ inline int chunks_block_smem(const ChunkStage& L) {
+    return 128 + STAGES * L.bytes + L.nch * 256 * UPL * 8;
+}
 
 }  // namespace gse

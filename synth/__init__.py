@@ -221,3 +221,8 @@ def batch_specs(count: int = 512, seed: int = 0, n_lo: float = 1e3, n_hi: float 
         shift = float(np.exp(rng.uniform(np.log(1e-4), np.log(1e-1))))
         out.append(SystemSpec(d, (side,) * d, aniso, shift))
     return out
+
+
+def shard_specs(specs: list, rank: int, world: int) -> list:
+    """The systems one of `world` replicas solves (round robin)."""
+    return specs[rank::world]

@@ -163,3 +163,38 @@ def test_stepped_cg_on_each_engine_schedule(sched):
     assert info["status"] == gse.OK and info["k_final"] == 3 and info["rel_res_true"] < 1e-10
     assert abs(info["iters"] - ref["info"]["iters"]) <= 3
     assert np.max(np.abs(x.cpu().numpy() - ref["x"])) < 1e-8
+
+
+def test_server_mixed_stream_equals_solo():
+    """Served solves (continuous batching, admission by a memory budget that
+    lets only a few systems in at once) give the solo results bit for bit."""
+    from paper_2411_04686_gb300 import serve
+    As = _systems(9, 8)
+    pool = [(A, synth.rhs_ones(A)) for A in As]
+    budget = 3 * max(serve.estimate_footprint(A.n_rows, A.nnz) for A in As)
+    srv = serve.Server(lambda i: pool[i], capacity=8, mem_budget=budget, slots_per_step=5)
+    for i, A in enumerate(As):
+        srv.submit(serve.Request(i, 0.0, A.n_rows, A.nnz, payload=i))
+    xs = {}
+    orig = srv.place
+
+    def place(A, b):
+        M, bd, x = orig(A, b)
+        xs[id(A)] = x
+        return M, bd, x
+
+    srv.place = place
+    peak = 0
+    while srv.queue or srv.active:
+        srv.step()
+        peak = max(peak, len(srv.active))
+        assert srv.used <= budget             # admission never exceeds the memory budget
+    srv.close()
+    assert 1 < peak < len(As) and len(srv.done) == len(As)
+    for c in srv.done:
+        A, b = pool[c.rid]
+        M = gse.GseMatrix.from_csr(A)
+        x1 = torch.zeros(A.n_rows, dtype=torch.float64, device="cuda")
+        i1 = M.cg(_dev(b), x1)
+        assert c.info["status"] == gse.OK and c.info["iters"] == i1["iters"]
+        assert torch.equal(xs[id(A)], x1)

@@ -100,8 +100,7 @@ def test_full_size_sampled_rows(which):
     """The benchmark matrices at full size, in the launch configuration the
     benchmark times: 4000 sampled rows checked against the oracle."""
     A = synth.laplace3d(128) if which == "laplace3d_128" else synth.powerlaw_random(1_000_000, 16.0, 2048, seed=0)
-    M = gse.GseMatrix.from_csr(A, attach=(64, 32))
-    M.autotune(1)                  # the schedule the benchmark runs
+    M = gse.GseMatrix.from_csr(A, attach=(64, 32))   # the schedule the benchmark runs (row statistics)
     x = synth.uniform_x(A.n_cols, seed=0)
     xd = torch.from_numpy(x).cuda()
     rng = np.random.default_rng(1)
@@ -113,6 +112,15 @@ def test_full_size_sampled_rows(which):
         check_spmv_rows(M.spmv(k, xd).cpu().numpy(), A, ak, x, rows=rows)
     check_spmv_rows(M.spmv(gse.LEVEL_FP64, xd).cpu().numpy(), A, A.val, x, rows=rows)
     M.free()
+
+
+def test_autotune_keeps_results_within_tolerance():
+    A = synth.powerlaw_random(30000, 16.0, 2048, seed=13)
+    M = gse.GseMatrix.from_csr(A)
+    M.autotune(2)
+    x = synth.uniform_x(A.n_cols, seed=4)
+    enc = oracle.encode(A.val)
+    check_spmv_rows(M.spmv(2, torch.from_numpy(x).cuda()).cpu().numpy(), A, oracle.decode(*enc, 2), x)
 
 
 def test_bad_level_rejected():

@@ -1,0 +1,114 @@
+"""Host logic of the serving loop, on the CPU with a fake clock, a fake memory
+budget and a fake engine: admission by footprint in arrival order, continuous
+batching (requests join as slots free up), latency bookkeeping, sharding."""
+from collections import deque
+
+import numpy as np
+import pytest
+
+from paper_2411_04686_gb300 import serve
+
+
+def test_admit_respects_slots_and_budget_in_order():
+    q = deque(serve.Request(i, float(i), 10, 50, footprint=f) for i, f in enumerate([40, 30, 50, 10]))
+    got = serve.admit(q, free_slots=3, free_bytes=80)
+    assert [r.rid for r in got] == [0, 1]          # 40 + 30 fit, 50 does not: it blocks request 3
+    assert [r.rid for r in q] == [2, 3]
+    assert serve.admit(q, free_slots=0, free_bytes=10**9) == []
+    assert [r.rid for r in serve.admit(q, 5, 60)] == [2, 3]
+
+
+def test_footprint_grows_with_size_and_method():
+    a = serve.estimate_footprint(1000, 5000)
+    b = serve.estimate_footprint(100000, 500000)
+    assert b > a > 5000 * 10
+    assert serve.estimate_footprint(1000, 5000, method="gmres") > a
+
+
+class FakeEngine:
+    """Each submitted system finishes after `need` slots of engine time."""
+
+    def __init__(self, capacity, need):
+        self.capacity, self.need = capacity, need
+        self.slots = {}
+        self.t = 0
+
+    def submit(self, M, b, x, tol, policy):
+        s = next(i for i in range(self.capacity) if i not in self.slots)
+        self.slots[s] = [self.need[M.rid], M.rid]
+        return s
+
+    def run(self, nslots, batch=8):
+        self.t += nslots
+        for v in self.slots.values():
+            v[0] -= nslots
+        return sum(1 for v in self.slots.values() if v[0] > 0)
+
+    def poll(self):
+        out = [(s, {"status": 0, "rid": v[1]}) for s, v in self.slots.items() if v[0] <= 0]
+        for s, _ in out:
+            del self.slots[s]
+        return out
+
+    def close(self):
+        pass
+
+
+class FakeMatrix:
+    def __init__(self, rid):
+        self.rid = rid
+        self.freed = False
+
+    def free(self):
+        self.freed = True
+
+
+def test_continuous_batching_with_fake_engine_and_clock():
+    need = {0: 30, 1: 10, 2: 10, 3: 10, 4: 5}
+    eng = FakeEngine(2, need)
+    clock = {"t": 0.0}
+    placed = []
+
+    def place(A, b):
+        m = FakeMatrix(A)
+        placed.append(m)
+        return m, None, None
+
+    srv = serve.Server(build=lambda rid: (rid, None), capacity=2, mem_budget=100, slots_per_step=10,
+                       clock=lambda: clock["t"], engine=eng, place=place)
+    for rid in range(5):
+        srv.submit(serve.Request(rid, 0.0, 1, 1, payload=rid, footprint=40))
+    order = []
+    while srv.queue or srv.active:
+        clock["t"] += 1.0
+        srv.step()
+        order = [c.rid for c in srv.done]
+    # two slots and a budget for two: 0 and 1 start; 1 leaves after one step, 2 joins
+    # while 0 is still running (continuous batching), and so on
+    assert order == [1, 2, 0, 3, 4]
+    assert all(m.freed for m in placed)
+    assert srv.used == 0
+    lat = serve.latency_stats(srv.done)
+    assert lat["n"] == 5 and lat["p50_s"] > 0
+
+
+def test_memory_budget_limits_concurrency():
+    eng = FakeEngine(8, {i: 10 for i in range(6)})
+    peak = {"v": 0}
+    srv = serve.Server(build=lambda rid: (rid, None), capacity=8, mem_budget=100, slots_per_step=10,
+                       clock=lambda: 0.0, engine=eng, place=lambda A, b: (FakeMatrix(A), None, None))
+    for rid in range(6):
+        srv.submit(serve.Request(rid, 0.0, 1, 1, payload=rid, footprint=45))
+    while srv.queue or srv.active:
+        srv.step()
+        peak["v"] = max(peak["v"], len(srv.active))
+    assert peak["v"] <= 2 and len(srv.done) == 6
+
+
+def test_poisson_arrivals_and_shard():
+    t = serve.poisson_arrivals(20000, rate=100.0, seed=0)
+    assert np.all(np.diff(t) > 0)
+    assert t[-1] / 20000 == pytest.approx(0.01, rel=0.05)
+    items = list(range(11))
+    parts = [serve.shard(items, r, 3) for r in range(3)]
+    assert sorted(sum(parts, [])) == items and all(parts)
