@@ -115,21 +115,18 @@ extern "C" int gse_cg_noalloc(gse_handle h, const double* b, double* x, double t
     if (rc != GSE_OK) return rc;
 
     // the same partition the engine uses, so results match gse_cg bit for bit
-    int dev = 0, num_sms = 1, resident = 1;
+    int dev = 0, num_sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute((const void*)k_cg_p1, cudaFuncAttributeMaxDynamicSharedMemorySize, ENG_WARPS * eng_max_warp_smem());
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_cg_p1, ENG_WARPS * 32, p1_smem()) != cudaSuccess ||
-        resident < 1)
-        resident = 1;
     SysDesc d;
     memset(&d, 0, sizeof(d));
     d.m = h->v;
     d.err = h->d_err;
-    sys_partition(d, h, num_sms, resident);
+    sys_partition(d, h, num_sms);
     const int64_t nbs = d.nblk_spmv, nbv = d.nblk_vec;
     if (nbs > NA_MAX_BLOCKS || nbv > NA_MAX_BLOCKS) return GSE_ERR_UNSUPPORTED;
-    const int wsmem = sys_warp_smem(d);
+    const bool rows = d.sched == GSE_SCHEDULE_ROWS;
+    const size_t p1sm = rows ? p1_rows_smem(d.row_span, d.m.r_lo) : p1_smem();
     d.b = b;
     d.x = x;
     d.r = (double*)(base_ptr + NA_OFF_R);
@@ -177,8 +174,12 @@ extern "C" int gse_cg_noalloc(gse_handle h, const double* b, double* x, double t
     while (used < budget) {
         const int nb = budget - used < 16 ? budget - used : 16;
         for (int it = 0; it < nb; it++) {
-            k_cg_p1<<<(unsigned)nbs, ENG_WARPS * 32, (size_t)ENG_WARPS * wsmem, s>>>(d_sys, map_spmv, wsmem);
-            k_cg_fix<<<(unsigned)nbv, 256, 0, s>>>(d_sys, map_vec);
+            if (rows) {
+                k_cg_p1_rows<<<(unsigned)nbs, ENG_ROW_WARPS * 32, p1sm, s>>>(d_sys, map_spmv);
+            } else {
+                k_cg_p1<<<(unsigned)nbs, ENG_WARPS * 32, p1sm, s>>>(d_sys, map_spmv);
+                k_cg_fix<<<(unsigned)nbv, 256, 0, s>>>(d_sys, map_vec);
+            }
             k_cg_p2<<<(unsigned)nbv, 256, 0, s>>>(d_sys, map_vec);
             k_cg_p3<<<(unsigned)nbv, 256, 0, s>>>(d_sys, map_vec);
         }

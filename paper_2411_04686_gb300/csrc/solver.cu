@@ -57,6 +57,20 @@ __device__ __forceinline__ bool sys_grid_sum(double v, double* partial, unsigned
     return true;
 }
 
+// Same block bookkeeping without a sum: true in the last block of the system.
+__device__ __forceinline__ bool sys_grid_last(unsigned* counter, int nblk) {
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(counter, 1u) == (unsigned)nblk - 1;
+    }
+    __syncthreads();
+    if (!last) return false;
+    if (threadIdx.x == 0) *counter = 0;
+    return true;
+}
+
 // ITER: q = A p with the p.q epilogue; RESID: y = b - A x, no dot.  The engine
 // runs one unit of 8 nonzeros per lane (chunks of 256), ENG_WARPS chunks per stage.
 template <bool ITER>
@@ -75,20 +89,24 @@ template <bool ITER>
 __device__ __forceinline__ double eng_rows(int k, const MatView& m, const double* x, const Epi& e, int64_t sb0,
                                            int64_t sbs, int64_t nsb, int span, unsigned char* smem, int* err) {
     switch (k) {
-        case 1: return spmv_rows_block<1, 0, ITER, !ITER, ENG_STAGES>(m, x, e, sb0, sbs, nsb, row_stage_layout<1, 0>(span, m.r_lo), smem, err);
-        case 2: return spmv_rows_block<2, 0, ITER, !ITER, ENG_STAGES>(m, x, e, sb0, sbs, nsb, row_stage_layout<2, 0>(span, m.r_lo), smem, err);
-        case 3: return spmv_rows_block<3, -1, ITER, !ITER, ENG_STAGES>(m, x, e, sb0, sbs, nsb, row_stage_layout<3, -1>(span, m.r_lo), smem, err);
-        case SRC_FP32: return spmv_rows_block<SRC_FP32, 0, ITER, !ITER, ENG_STAGES>(m, x, e, sb0, sbs, nsb, row_stage_layout<SRC_FP32, 0>(span, m.r_lo), smem, err);
-        default: return spmv_rows_block<SRC_FP64, 0, ITER, !ITER, ENG_STAGES>(m, x, e, sb0, sbs, nsb, row_stage_layout<SRC_FP64, 0>(span, m.r_lo), smem, err);
+        case 1: return spmv_rows_block<1, 0, ITER, !ITER, ENG_ROW_STAGES>(m, x, e, sb0, sbs, nsb, row_stage_layout<1, 0>(span, m.r_lo), smem, err);
+        case 2: return spmv_rows_block<2, 0, ITER, !ITER, ENG_ROW_STAGES>(m, x, e, sb0, sbs, nsb, row_stage_layout<2, 0>(span, m.r_lo), smem, err);
+        case 3:
+            if (m.r_lo == 4)
+                return spmv_rows_block<3, 4, ITER, !ITER, ENG_ROW_STAGES>(m, x, e, sb0, sbs, nsb, row_stage_layout<3, -1>(span, m.r_lo), smem, err);
+            return spmv_rows_block<3, -1, ITER, !ITER, ENG_ROW_STAGES>(m, x, e, sb0, sbs, nsb, row_stage_layout<3, -1>(span, m.r_lo), smem, err);
+        case SRC_FP32: return spmv_rows_block<SRC_FP32, 0, ITER, !ITER, ENG_ROW_STAGES>(m, x, e, sb0, sbs, nsb, row_stage_layout<SRC_FP32, 0>(span, m.r_lo), smem, err);
+        default: return spmv_rows_block<SRC_FP64, 0, ITER, !ITER, ENG_ROW_STAGES>(m, x, e, sb0, sbs, nsb, row_stage_layout<SRC_FP64, 0>(span, m.r_lo), smem, err);
     }
 }
 
 // ---- P1: SpMV phase -------------------------------------------------------
+// Two kernels, one per schedule, so the row kernel keeps the register budget
+// and CTA shape (8 warps, 256-row super-blocks) of the standalone row SpMV.
 
-__global__ void __launch_bounds__(ENG_WARPS * 32) k_cg_p1(const SysDesc* __restrict__ sys,
-                                                           const int2* __restrict__ map, int warp_smem) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ double red[32];
+template <bool ROWS>
+__device__ __forceinline__ void p1_body(const SysDesc* __restrict__ sys, const int2* __restrict__ map,
+                                        unsigned char* smem, double* red) {
     const int2 bm = map[blockIdx.x];
     const SysDesc& S = sys[bm.x];
     CgState* st = S.st;
@@ -106,19 +124,37 @@ __global__ void __launch_bounds__(ENG_WARPS * 32) k_cg_p1(const SysDesc* __restr
     } else {
         e.kind = EPI_RESID; e.y = S.q; e.b = S.b; e.p = nullptr; x = S.x; k = S.prm.kmax;
     }
-    (void)warp_smem;
-    const bool rows = S.sched == GSE_SCHEDULE_ROWS;
-    const int64_t nsb = (S.n + 32 * ENG_WARPS - 1) / (32 * ENG_WARPS);
-    if (!rows) fill_empty_rows(m, e, (int64_t)lb * blockDim.x + threadIdx.x, (int64_t)nblk * blockDim.x);
+    const int64_t nsb = (S.n + 32 * ENG_ROW_WARPS - 1) / (32 * ENG_ROW_WARPS);
+    if (!ROWS) fill_empty_rows(m, e, (int64_t)lb * blockDim.x + threadIdx.x, (int64_t)nblk * blockDim.x);
     if (mode == MODE_ITER) {
-        const double dot = rows ? eng_rows<true>(k, m, x, e, lb, nblk, nsb, S.row_span, smem, S.err)
+        const double dot = ROWS ? eng_rows<true>(k, m, x, e, lb, nblk, nsb, S.row_span, smem, S.err)
                                 : eng_pipe<true>(k, m, x, e, lb, nblk, S.n_chunks, smem, S.err);
         double total;
-        if (sys_grid_sum(dot, S.partial, S.counter, lb, nblk, red, &total) && threadIdx.x == 0) st->pq = total;
+        if (sys_grid_sum(dot, S.partial, S.counter, lb, nblk, red, &total) && threadIdx.x == 0) {
+            // alpha = rho / p.Ap once per system here, not in every thread of P2
+            const double alpha = st->rho / total;
+            st->pq = total;
+            st->alpha = alpha;
+            st->brk = !(total > 0.0) || !isfinite(total) || !isfinite(alpha);
+        }
     } else {
-        if (rows) eng_rows<false>(k, m, x, e, lb, nblk, nsb, S.row_span, smem, S.err);
+        if (ROWS) eng_rows<false>(k, m, x, e, lb, nblk, nsb, S.row_span, smem, S.err);
         else eng_pipe<false>(k, m, x, e, lb, nblk, S.n_chunks, smem, S.err);
     }
+}
+
+__global__ void __launch_bounds__(ENG_WARPS * 32) k_cg_p1(const SysDesc* __restrict__ sys,
+                                                           const int2* __restrict__ map) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ double red[32];
+    p1_body<false>(sys, map, smem, red);
+}
+
+__global__ void __launch_bounds__(ENG_ROW_WARPS * 32, 4) k_cg_p1_rows(const SysDesc* __restrict__ sys,
+                                                                    const int2* __restrict__ map) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ double red[32];
+    p1_body<true>(sys, map, smem, red);
 }
 
 // ---- P1b: rows that cross chunks (after P1) --------------------------------
@@ -198,13 +234,25 @@ __global__ void __launch_bounds__(256) k_cg_p2(const SysDesc* __restrict__ sys, 
     double acc = 0.0, alpha = 0.0;
     bool brk = false;
     if (mode == MODE_ITER) {
-        const double pq = st->pq;
-        alpha = st->rho / pq;
-        brk = !(pq > 0.0) || !isfinite(pq) || !isfinite(alpha);
+        alpha = st->alpha;
+        brk = st->brk != 0;
         if (!brk) {
             double* __restrict__ r = S.r;
             const double* __restrict__ q = S.q;
-            for (int64_t i = (int64_t)lb * blockDim.x + threadIdx.x; i < n; i += (int64_t)nblk * blockDim.x) {
+            const int64_t di = (int64_t)nblk * blockDim.x;
+            int64_t i = (int64_t)lb * blockDim.x + threadIdx.x;
+            for (; i + 3 * di < n; i += 4 * di) {      // four elements' loads in flight
+                double rv[4], qv[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) { rv[u] = r[i + u * di]; qv[u] = q[i + u * di]; }
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const double ri = fma(-alpha, qv[u], rv[u]);
+                    r[i + u * di] = ri;
+                    acc = fma(ri, ri, acc);
+                }
+            }
+            for (; i < n; i += di) {
                 const double ri = fma(-alpha, q[i], r[i]);
                 r[i] = ri;
                 acc = fma(ri, ri, acc);
@@ -218,7 +266,19 @@ __global__ void __launch_bounds__(256) k_cg_p2(const SysDesc* __restrict__ sys, 
     double total;
     if (!sys_grid_sum(acc, S.partial, S.counter + 1, lb, nblk, red, &total)) return;
     // ---- last block of this system: the decisions ----
-    const CgParams& P = S.prm;
+    // The state and parameters are brought into shared memory with one
+    // parallel load, decided on there, and written back with one parallel
+    // store: no chain of dependent global round trips in the serial part.
+    __shared__ CgState ss;
+    __shared__ CgParams sp;
+    static_assert(sizeof(CgState) % 8 == 0 && sizeof(CgParams) % 8 == 0, "word copies");
+    constexpr int NS = sizeof(CgState) / 8, NP = sizeof(CgParams) / 8;
+    if (threadIdx.x < NS) reinterpret_cast<long long*>(&ss)[threadIdx.x] = __ldcg(reinterpret_cast<const long long*>(S.st) + threadIdx.x);
+    else if (threadIdx.x < NS + NP)
+        reinterpret_cast<long long*>(&sp)[threadIdx.x - NS] = reinterpret_cast<const long long*>(&S.prm)[threadIdx.x - NS];
+    __syncthreads();
+    st = &ss;
+    const CgParams& P = sp;
     if (threadIdx.x == 0) {
         need_metrics = 0;
         if (mode == MODE_ITER) {
@@ -307,6 +367,8 @@ __global__ void __launch_bounds__(256) k_cg_p2(const SysDesc* __restrict__ sys, 
             }
         }
     }
+    __syncthreads();
+    if (threadIdx.x < NS) reinterpret_cast<long long*>(S.st)[threadIdx.x] = reinterpret_cast<const long long*>(&ss)[threadIdx.x];
 }
 
 // ---- P3: x and p updates --------------------------------------------------
@@ -327,19 +389,34 @@ __global__ void __launch_bounds__(256) k_cg_p3(const SysDesc* __restrict__ sys, 
     const double* __restrict__ q = S.q;
     double acc = 0.0;
     const int64_t i0 = (int64_t)lb * blockDim.x + threadIdx.x, di = (int64_t)nblk * blockDim.x;
+    // ||x||^2 feeds only the floor rule (GSE_POLICY_FLOOR); FP64 issue is scarce
+    const bool xn = (S.prm.flags & GSE_POLICY_FLOOR) != 0;
     if (pa == PA_UPDATE) {
-        for (int64_t i = i0; i < n; i += di) {
+        int64_t i = i0;
+        for (; i + 3 * di < n; i += 4 * di) {          // four elements' loads in flight
+            double pv[4], xv[4], rv[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) { pv[u] = p[i + u * di]; xv[u] = x[i + u * di]; rv[u] = r[i + u * di]; }
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const double xi = fma(alpha, pv[u], xv[u]);
+                x[i + u * di] = xi;
+                p[i + u * di] = fma(beta, pv[u], rv[u]);
+                if (xn) acc = fma(xi, xi, acc);
+            }
+        }
+        for (; i < n; i += di) {
             const double pi = p[i];
             const double xi = fma(alpha, pi, x[i]);
             x[i] = xi;
             p[i] = fma(beta, pi, r[i]);
-            acc = fma(xi, xi, acc);
+            if (xn) acc = fma(xi, xi, acc);
         }
     } else if (pa == PA_XONLY) {
         for (int64_t i = i0; i < n; i += di) {
             const double xi = fma(alpha, p[i], x[i]);
             x[i] = xi;
-            acc = fma(xi, xi, acc);
+            if (xn) acc = fma(xi, xi, acc);
         }
     } else if (pa == PA_COPY_R) {
         for (int64_t i = i0; i < n; i += di) p[i] = r[i];
@@ -352,10 +429,14 @@ __global__ void __launch_bounds__(256) k_cg_p3(const SysDesc* __restrict__ sys, 
     } else {
         for (int64_t i = i0; i < n; i += di) x[i] = 0.0;
     }
-    double total;
-    if (!sys_grid_sum(acc, S.partial, S.counter + 2, lb, nblk, red, &total)) return;
+    double total = 0.0;
+    if (xn) {
+        if (!sys_grid_sum(acc, S.partial, S.counter + 2, lb, nblk, red, &total)) return;
+    } else if (!sys_grid_last(S.counter + 2, nblk)) {
+        return;
+    }
     if (threadIdx.x == 0) {
-        if (pa == PA_UPDATE || pa == PA_XONLY) st->xnorm2 = total;
+        if (xn && (pa == PA_UPDATE || pa == PA_XONLY)) st->xnorm2 = total;
         st->p_action = PA_NONE;
     }
 }
@@ -500,16 +581,16 @@ struct gse_cg_engine {
     cudaStream_t stream = nullptr;
     int device = 0;
     int num_sms = 1;
-    int p1_resident = 1;
     SysDesc* d_sys = nullptr;
     CgState* d_state = nullptr;
     CgState* h_state = nullptr;    // pinned mirror (latest completed batch)
     CgState* h_stage[2] = {nullptr, nullptr};  // pinned landing buffers, one per batch in flight
-    int2* d_map_spmv = nullptr;
+    int2* d_map_spmv = nullptr;     // P1 blocks of nonzero-split systems
+    int2* d_map_rows = nullptr;     // P1 blocks of row-schedule systems
     int2* d_map_vec = nullptr;
-    int map_cap_spmv = 0, map_cap_vec = 0;
-    int nblk_spmv = 0, nblk_vec = 0;
-    int warp_smem = 0;
+    int map_cap_spmv = 0, map_cap_rows = 0, map_cap_vec = 0;
+    int nblk_spmv = 0, nblk_rows = 0, nblk_vec = 0;
+    size_t rows_smem = 0;           // dynamic shared memory of the row P1 launch (widest system)
     std::vector<EngineSlot> slots;
     std::vector<SysDesc> h_sys;
     bool dirty = true;
@@ -525,11 +606,8 @@ extern "C" int gse_engine_create(int capacity, void* stream, gse_engine* out) {
     e->stream = (cudaStream_t)stream;
     cudaGetDevice(&e->device);
     cudaDeviceGetAttribute(&e->num_sms, cudaDevAttrMultiProcessorCount, e->device);
-    cudaFuncSetAttribute((const void*)k_cg_p1, cudaFuncAttributeMaxDynamicSharedMemorySize, ENG_WARPS * eng_max_warp_smem());
-    int nb = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cg_p1, ENG_WARPS * 32, p1_smem()) != cudaSuccess || nb < 1)
-        nb = 1;
-    e->p1_resident = nb;
+    p1_occupancy(false, p1_smem());     // sets both kernels' shared-memory limits
+    p1_occupancy(true, p1_rows_smem_max());
     e->slots.resize(capacity);
     e->h_sys.resize(capacity);
     if (cudaMalloc(&e->d_sys, capacity * sizeof(SysDesc)) != cudaSuccess ||
@@ -557,6 +635,7 @@ extern "C" void gse_engine_destroy(gse_engine e) {
     if (e->h_stage[0]) cudaFreeHost(e->h_stage[0]);
     if (e->h_stage[1]) cudaFreeHost(e->h_stage[1]);
     if (e->d_map_spmv) cudaFree(e->d_map_spmv);
+    if (e->d_map_rows) cudaFree(e->d_map_rows);
     if (e->d_map_vec) cudaFree(e->d_map_vec);
     if (e->ev[0]) cudaEventDestroy(e->ev[0]);
     if (e->ev[1]) cudaEventDestroy(e->ev[1]);
@@ -595,7 +674,7 @@ extern "C" int gse_engine_submit(gse_engine e, gse_handle h, const double* b, do
     memset(&d, 0, sizeof(d));
     d.m = h->v;
     d.err = h->d_err;
-    sys_partition(d, h, e->num_sms, e->p1_resident);
+    sys_partition(d, h, e->num_sms);
     if (d.nblk_spmv > w->partial_cap || d.nblk_vec > w->partial_cap) return GSE_ERR_INVALID;
     d.b = b;
     d.x = x;
@@ -642,13 +721,14 @@ extern "C" int gse_engine_submit(gse_engine e, gse_handle h, const double* b, do
 }
 
 static int rebuild_maps(gse_cg_engine* e) {
-    std::vector<int2> ms, mv;
-    int wsm = ENG_WARP_SMEM;
+    std::vector<int2> ms, mr, mv;
+    size_t rsm = 0;
     for (int i = 0; i < e->capacity; i++) {
         if (!e->slots[i].active) continue;
         const SysDesc& d = e->h_sys[i];
-        if (sys_warp_smem(d) > wsm) wsm = sys_warp_smem(d);
-        for (int b = 0; b < d.nblk_spmv; b++) ms.push_back(make_int2(i, b));
+        const bool rows = d.sched == GSE_SCHEDULE_ROWS;
+        if (rows && p1_rows_smem(d.row_span, d.m.r_lo) > rsm) rsm = p1_rows_smem(d.row_span, d.m.r_lo);
+        for (int b = 0; b < d.nblk_spmv; b++) (rows ? mr : ms).push_back(make_int2(i, b));
         for (int b = 0; b < d.nblk_vec; b++) mv.push_back(make_int2(i, b));
     }
     auto grow = [](int2** buf, int* cap, size_t need) -> int {
@@ -661,22 +741,28 @@ static int rebuild_maps(gse_cg_engine* e) {
     };
     cudaStreamSynchronize(e->stream);
     int rc = grow(&e->d_map_spmv, &e->map_cap_spmv, ms.size());
+    if (rc == GSE_OK) rc = grow(&e->d_map_rows, &e->map_cap_rows, mr.size());
     if (rc == GSE_OK) rc = grow(&e->d_map_vec, &e->map_cap_vec, mv.size());
     if (rc != GSE_OK) return rc;
     if (!ms.empty()) cudaMemcpy(e->d_map_spmv, ms.data(), ms.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    if (!mr.empty()) cudaMemcpy(e->d_map_rows, mr.data(), mr.size() * sizeof(int2), cudaMemcpyHostToDevice);
     if (!mv.empty()) cudaMemcpy(e->d_map_vec, mv.data(), mv.size() * sizeof(int2), cudaMemcpyHostToDevice);
     e->nblk_spmv = (int)ms.size();
+    e->nblk_rows = (int)mr.size();
     e->nblk_vec = (int)mv.size();
-    e->warp_smem = wsm;
+    e->rows_smem = rsm;
     e->dirty = false;
     return GSE_OK;
 }
 
 static void enqueue_slots(gse_cg_engine* e, int nslots) {
     for (int it = 0; it < nslots; it++) {
-        k_cg_p1<<<e->nblk_spmv, ENG_WARPS * 32, (size_t)ENG_WARPS * e->warp_smem, e->stream>>>(e->d_sys, e->d_map_spmv,
-                                                                                             e->warp_smem);
-        k_cg_fix<<<e->nblk_vec, 256, 0, e->stream>>>(e->d_sys, e->d_map_vec);
+        if (e->nblk_rows)
+            k_cg_p1_rows<<<e->nblk_rows, ENG_ROW_WARPS * 32, e->rows_smem, e->stream>>>(e->d_sys, e->d_map_rows);
+        if (e->nblk_spmv) {
+            k_cg_p1<<<e->nblk_spmv, ENG_WARPS * 32, p1_smem(), e->stream>>>(e->d_sys, e->d_map_spmv);
+            k_cg_fix<<<e->nblk_vec, 256, 0, e->stream>>>(e->d_sys, e->d_map_vec);   // split rows (nonzero split only)
+        }
         k_cg_p2<<<e->nblk_vec, 256, 0, e->stream>>>(e->d_sys, e->d_map_vec);
         k_cg_p3<<<e->nblk_vec, 256, 0, e->stream>>>(e->d_sys, e->d_map_vec);
     }

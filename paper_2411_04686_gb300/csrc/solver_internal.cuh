@@ -10,10 +10,12 @@ enum { MODE_ITER = 0, MODE_RESID_R = 1, MODE_RESID_T = 2, MODE_DONE = 3 };
 enum { PA_NONE = 0, PA_UPDATE = 1, PA_XONLY = 2, PA_COPY_R = 3, PA_COPY_Q = 4, PA_ZERO_X = 5 };
 constexpr int RING_MAX = 4096;
 constexpr int ENG_WARPS = 4;
-constexpr int ENG_STAGES = 3;
+constexpr int ENG_STAGES = 3;       // stage ring of the nonzero split
+constexpr int ENG_ROW_STAGES = 2;   // stage ring of the row schedule (wide stages: fewer, more CTAs)
+constexpr int ENG_ROW_WARPS = 8;    // row schedule: CTAs of 8 warps, 256-row super-blocks
 
 struct CgState {
-    int mode, k, status, j, p_action, hlen, hpos, pad;
+    int mode, k, status, j, p_action, hlen, hpos, brk;   // brk: p.Ap <= 0 or non-finite (set by P1)
     int sw[4];
     double rho, pq, alpha, beta, nb, res, true_res, xnorm2;
 };
@@ -63,60 +65,68 @@ struct Workspace {
 // Engine kernels (solver.cu); one iteration slot is p1, fix, p2, p3.  Each processes the systems named by `map`
 // (one int2 {system, block-within-system} per block).
 __global__ void k_cg_init(const SysDesc* __restrict__ sys, const int2* __restrict__ map);
-__global__ void k_cg_p1(const SysDesc* __restrict__ sys, const int2* __restrict__ map, int warp_smem);
+__global__ void k_cg_p1(const SysDesc* __restrict__ sys, const int2* __restrict__ map);        // nonzero split
+__global__ void k_cg_p1_rows(const SysDesc* __restrict__ sys, const int2* __restrict__ map);   // row schedule
 __global__ void k_cg_fix(const SysDesc* __restrict__ sys, const int2* __restrict__ map);
 __global__ void k_cg_p2(const SysDesc* __restrict__ sys, const int2* __restrict__ map);
 __global__ void k_cg_p3(const SysDesc* __restrict__ sys, const int2* __restrict__ map);
 
-// Per-warp share of P1's shared memory on the nonzero split: the CTA's stage
-// ring for the largest value source, divided over its warps.
-inline int eng_chunks_warp_smem() {
+// Shared memory of a P1 CTA on the nonzero split: the stage ring for the
+// largest value source (a system's level changes during the solve).
+inline size_t p1_smem() {
     const int a = chunks_block_smem<ENG_STAGES, 1>(chunk_stage_layout<SRC_FP64, 0, 1>(ENG_WARPS, 16));
     const int b = chunks_block_smem<ENG_STAGES, 1>(chunk_stage_layout<3, -1, 1>(ENG_WARPS, 16));
-    return ((a > b ? a : b) + ENG_WARPS - 1) / ENG_WARPS;
-}
-#define ENG_WARP_SMEM (eng_chunks_warp_smem())
-inline size_t p1_smem() { return (size_t)ENG_WARPS * ENG_WARP_SMEM; }
-
-// Largest per-warp shared memory P1 can need (row schedule at the widest span).
-inline int eng_max_warp_smem() {
-    const int r = rows_block_smem<ENG_STAGES>(row_stage_layout<SRC_FP64, 0>(GSE_ROW_SPAN_MAX, 16));
-    const int q = rows_block_smem<ENG_STAGES>(row_stage_layout<3, -1>(GSE_ROW_SPAN_MAX, 16));
-    const int m = (r > q ? r : q) / ENG_WARPS + 1;
-    return m > ENG_WARP_SMEM ? m : ENG_WARP_SMEM;
+    return (size_t)(a > b ? a : b);
 }
 
-// Per-warp shared memory P1 needs for a system (its schedule, any level).
-// (The row schedule stages whole CTAs: its need is the CTA's, divided over the warps.)
-inline int sys_warp_smem(const SysDesc& d) {
-    if (d.sched != GSE_SCHEDULE_ROWS) return ENG_WARP_SMEM;
-    const int a = rows_block_smem<ENG_STAGES>(row_stage_layout<SRC_FP64, 0>(d.row_span, d.m.r_lo));
-    const int b = rows_block_smem<ENG_STAGES>(row_stage_layout<3, -1>(d.row_span, d.m.r_lo));
-    const int need = (a > b ? a : b);
-    return (need + ENG_WARPS - 1) / ENG_WARPS;
+// Shared memory of a P1 CTA on the row schedule for a stage span (nonzeros per
+// 256-row super-block), again for the largest value source.
+inline size_t p1_rows_smem(int span, int r_lo) {
+    const int a = rows_block_smem<ENG_ROW_STAGES>(row_stage_layout<SRC_FP64, 0>(span, r_lo));
+    const int b = rows_block_smem<ENG_ROW_STAGES>(row_stage_layout<3, -1>(span, r_lo));
+    return (size_t)(a > b ? a : b);
+}
+inline size_t p1_rows_smem_max() { return p1_rows_smem(GSE_ROW_SPAN_MAX, 16); }
+
+// P1 CTAs an SM holds for a dynamic shared-memory size (row or nonzero-split kernel).
+inline int p1_occupancy(bool rows, size_t smem) {
+    const void* fn = rows ? (const void*)k_cg_p1_rows : (const void*)k_cg_p1;
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(rows ? p1_rows_smem_max() : p1_smem()));
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, (rows ? ENG_ROW_WARPS : ENG_WARPS) * 32, smem) !=
+            cudaSuccess ||
+        nb < 1)
+        nb = 1;
+    return nb;
 }
 
 // Fills the schedule-dependent part of a system descriptor (engine and
 // allocation-free entry point use the same partition, so results match).
-inline void sys_partition(SysDesc& d, const gse_matrix* h, int num_sms, int p1_resident) {
+// Block counts depend on the system and the device only, never on what else
+// is in a batch: P1 gets one wave of CTAs at the occupancy of the system's own
+// stage ring (row schedule) or of the nonzero-split ring.
+inline void sys_partition(SysDesc& d, const gse_matrix* h, int num_sms) {
     d.upl = 1;
-    d.row_span = h->row_span128;   // super-blocks of 32 * ENG_WARPS = 128 rows
+    d.row_span = h->row_span256;   // super-blocks of 32 * ENG_ROW_WARPS = 256 rows
     d.sched = (h->schedule_forced ? h->schedule_forced : h->schedule_auto) == GSE_SCHEDULE_ROWS &&
-                      h->row_span128 <= GSE_ROW_SPAN_MAX ? GSE_SCHEDULE_ROWS : 1;
+                      h->row_span256 <= GSE_ROW_SPAN_MAX ? GSE_SCHEDULE_ROWS : 1;
     d.n = h->v.n_rows;
     d.n_chunks = (h->v.nnz + 255) / 256;
     const int64_t partial_cap = (int64_t)num_sms * 64;
     int64_t nbs;
     if (d.sched == GSE_SCHEDULE_ROWS) {
-        nbs = (d.n + 32 * ENG_WARPS - 1) / (32 * ENG_WARPS);
-        if (nbs > (int64_t)num_sms * 4) nbs = (int64_t)num_sms * 4;   // fixed cap: independent of the batch
+        nbs = (d.n + 32 * ENG_ROW_WARPS - 1) / (32 * ENG_ROW_WARPS);
+        const int64_t wave = (int64_t)num_sms * p1_occupancy(true, p1_rows_smem(d.row_span, d.m.r_lo));
+        if (nbs > wave) nbs = wave;
     } else {
         nbs = (d.n_chunks + ENG_WARPS - 1) / ENG_WARPS;                // super-chunks
-        if (nbs > (int64_t)num_sms * p1_resident) nbs = (int64_t)num_sms * p1_resident;
+        const int64_t wave = (int64_t)num_sms * p1_occupancy(false, p1_smem());
+        if (nbs > wave) nbs = wave;
     }
     if (nbs < 1) nbs = 1;
     int64_t nbv = (d.n + 1023) / 1024;
-    if (nbv > (int64_t)num_sms * 8) nbv = (int64_t)num_sms * 8;
+    if (nbv > (int64_t)num_sms * 4) nbv = (int64_t)num_sms * 4;   // fewer partial sums: FP64 adds are scarce
     if (nbv < 1) nbv = 1;
     if (nbs > partial_cap) nbs = partial_cap;
     if (nbv > partial_cap) nbv = partial_cap;

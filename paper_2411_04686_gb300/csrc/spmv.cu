@@ -34,42 +34,76 @@ __global__ void __launch_bounds__(256) k_spmv_fix(MatView m, Epi e, int64_t n_ch
 }
 
 // Row schedule: one row per lane, 256 consecutive rows per CTA and stage,
-// staged by one producer thread with large bulk copies (short rows).
+// staged by one producer thread with large bulk copies (short rows).  The ring
+// has 2 or 3 stages, whichever keeps more warps resident (wide stages at k = 3
+// and FP64 cap the CTAs an SM holds by shared memory).
 constexpr int ROWS_WARPS = 8;
-constexpr int ROWS_STAGES = 3;
 
-template <int K, int R, bool RESID>
+template <int K, int R, bool RESID, int STAGES>
 __global__ void __launch_bounds__(ROWS_WARPS * 32) k_spmv_rows(MatView m, const double* __restrict__ x, Epi e,
                                                                 int64_t nsb, RowStage L, int* err, const int* gate) {
     if (gate && *gate) return;
     extern __shared__ __align__(128) unsigned char smem[];
-    spmv_rows_block<K, R, false, RESID, ROWS_STAGES>(m, x, e, blockIdx.x, gridDim.x, nsb, L, smem, err);
+    spmv_rows_block<K, R, false, RESID, STAGES>(m, x, e, blockIdx.x, gridDim.x, nsb, L, smem, err);
 }
 
 typedef void (*RowsKernel)(MatView, const double*, Epi, int64_t, RowStage, int*, const int*);
 
-template <bool RESID>
+template <bool RESID, int STAGES>
 static RowsKernel pick_rows_t(int k, int r_lo, RowStage* L, int span) {
     switch (k) {
-        case 1: *L = row_stage_layout<1, 0>(span, r_lo); return k_spmv_rows<1, 0, RESID>;
-        case 2: *L = row_stage_layout<2, 0>(span, r_lo); return k_spmv_rows<2, 0, RESID>;
-        case 3: *L = row_stage_layout<3, -1>(span, r_lo); return k_spmv_rows<3, -1, RESID>;
-        case SRC_FP32: *L = row_stage_layout<SRC_FP32, 0>(span, r_lo); return k_spmv_rows<SRC_FP32, 0, RESID>;
-        default: *L = row_stage_layout<SRC_FP64, 0>(span, r_lo); return k_spmv_rows<SRC_FP64, 0, RESID>;
+        case 1: *L = row_stage_layout<1, 0>(span, r_lo); return k_spmv_rows<1, 0, RESID, STAGES>;
+        case 2: *L = row_stage_layout<2, 0>(span, r_lo); return k_spmv_rows<2, 0, RESID, STAGES>;
+        case 3:
+            *L = row_stage_layout<3, -1>(span, r_lo);
+            if (r_lo == 4) return k_spmv_rows<3, 4, RESID, STAGES>;
+            if (r_lo == 0) return k_spmv_rows<3, 0, RESID, STAGES>;
+            return k_spmv_rows<3, -1, RESID, STAGES>;
+        case SRC_FP32: *L = row_stage_layout<SRC_FP32, 0>(span, r_lo); return k_spmv_rows<SRC_FP32, 0, RESID, STAGES>;
+        default: *L = row_stage_layout<SRC_FP64, 0>(span, r_lo); return k_spmv_rows<SRC_FP64, 0, RESID, STAGES>;
     }
 }
 
-static int launch_rows(gse_matrix* h, int k, int epi, const SpmvArgs& a, cudaStream_t s) {
-    RowStage L;
-    const bool resid = epi == EPI_RESID;
-    RowsKernel fn = resid ? pick_rows_t<true>(k, h->v.r_lo, &L, h->row_span256)
-                          : pick_rows_t<false>(k, h->v.r_lo, &L, h->row_span256);
-    const size_t smem = (size_t)rows_block_smem<ROWS_STAGES>(L);
-    if (smem > 48 * 1024)
-        cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+// Resident CTAs per SM of a row kernel with its shared memory (0 on error),
+// cached per (kernel, shared-memory size).
+static int rows_resident(RowsKernel fn, size_t smem) {
+    static std::mutex mu;
+    static const void* keys[256];
+    static size_t sizes[256];
+    static int vals[256];
+    static int nkeys = 0;
+    std::lock_guard<std::mutex> lock(mu);
+    for (int i = 0; i < nkeys; i++)
+        if (keys[i] == (const void*)fn && sizes[i] == smem) return vals[i];
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return 0;
     cudaFuncSetAttribute((const void*)fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, ROWS_WARPS * 32, smem) != cudaSuccess || nb < 1) nb = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, ROWS_WARPS * 32, smem) != cudaSuccess) return 0;
+    if (nkeys < 256) {
+        keys[nkeys] = (const void*)fn;
+        sizes[nkeys] = smem;
+        vals[nkeys] = nb;
+        nkeys++;
+    }
+    return nb;
+}
+
+static int launch_rows(gse_matrix* h, int k, int epi, const SpmvArgs& a, cudaStream_t s) {
+    RowStage L2, L3;
+    const bool resid = epi == EPI_RESID;
+    RowsKernel f3 = resid ? pick_rows_t<true, 3>(k, h->v.r_lo, &L3, h->row_span256)
+                          : pick_rows_t<false, 3>(k, h->v.r_lo, &L3, h->row_span256);
+    RowsKernel f2 = resid ? pick_rows_t<true, 2>(k, h->v.r_lo, &L2, h->row_span256)
+                          : pick_rows_t<false, 2>(k, h->v.r_lo, &L2, h->row_span256);
+    const size_t smem3 = (size_t)rows_block_smem<3>(L3), smem2 = (size_t)rows_block_smem<2>(L2);
+    const int nb3 = rows_resident(f3, smem3), nb2 = rows_resident(f2, smem2);
+    const bool two = nb2 > nb3;
+    RowsKernel fn = two ? f2 : f3;
+    const size_t smem = two ? smem2 : smem3;
+    const RowStage L = two ? L2 : L3;
+    const int nb = (two ? nb2 : nb3) < 1 ? 1 : (two ? nb2 : nb3);
     const int64_t nsb = (h->v.n_rows + 32 * ROWS_WARPS - 1) / (32 * ROWS_WARPS);
     int64_t g = nsb;
     const int64_t resident = (int64_t)h->num_sms * nb;

@@ -82,6 +82,28 @@ __device__ __forceinline__ double decode_l3(uint32_t h, uint32_t t1, uint32_t t2
     return M ? __longlong_as_double((long long)bits) : __longlong_as_double((long long)((uint64_t)sign << 63));
 }
 
+// Level 3 when the leading one of M_3 lies in the head (head magnitude != 0)
+// and the tails fit below bit 52 (W_3 <= 52): the FP32 image of the head gives
+// the exponent and the top mantissa bits exactly as at level 1 (the value's
+// leading one is the head's at every level), and the tails T = t1 << s3 | t2
+// are shifted in right below it -- no 64-bit CLZ, no data-dependent shift
+// direction.  Bit-identical to decode_l3 on the values it accepts; the caller
+// checks ok_l3_fast and falls back to decode_l3 otherwise.
+__device__ __forceinline__ bool ok_l3_fast(uint32_t h, int Eg, const MatView& m) {
+    return (h & ((1u << m.W1) - 1u)) != 0u && Eg > m.W1;
+}
+__device__ __forceinline__ double decode_l3_fast(uint32_t h, uint32_t t1, uint32_t t2, int Eg, const MatView& m) {
+    const uint32_t mag = h & ((1u << m.W1) - 1u);
+    const uint32_t fb = __float_as_uint(__uint_as_float(0x4B000000u | mag) - 8388608.0f);
+    // the leading one of M_3 sits at bit s2 + s3 + p, p = (fb >> 23) - 127; the
+    // tails go to mantissa bits below 52 - p, i.e. T << (52 - s2 - s3 - p)
+    const uint64_t T = ((uint64_t)t1 << m.s3) | t2;
+    const uint64_t low = T << ((179 - m.s2 - m.s3) - (int)(fb >> 23));
+    const uint32_t hi = (((fb >> 3) + ((uint32_t)(Eg - m.W1 - 127) << 20)) | ((h >> m.W1) << 31)) |
+                        (uint32_t)(low >> 32);
+    return __hiloint2double((int)hi, (int)(uint32_t)low);
+}
+
 // FP32 -> FP64 widening with integer operations (exact; no FP64 pipe use).
 __device__ __forceinline__ double widen_f32(uint32_t f) {
     const uint32_t sign = f & 0x80000000u;
@@ -159,7 +181,8 @@ __device__ __forceinline__ void load_unit(const MatView& m, int64_t u, int* col,
                         t2 = (t2 << m.r_lo) | ((lo[bit >> 5] >> (bit & 31)) & ((1u << m.r_lo) - 1u));
                     }
                 }
-                a[i] = decode_l3(h, u16_of(t1w, i), t2, Eg, m);
+                if ((R == 0 || R == 4) && ok_l3_fast(h, Eg, m)) a[i] = decode_l3_fast(h, u16_of(t1w, i), t2, Eg, m);
+                else a[i] = decode_l3(h, u16_of(t1w, i), t2, Eg, m);
             }
         }
     }

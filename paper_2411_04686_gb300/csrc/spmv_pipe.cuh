@@ -177,6 +177,7 @@ __device__ __forceinline__ double row_value(const MatView& m, const RowStage& L,
             const int bit = i * r;
             t2 = (t2 << r) | ((lw[bit >> 5] >> (bit & 31)) & ((1u << r) - 1u));
         }
+        if ((R == 0 || R == 4) && ok_l3_fast(h, Eg, m)) return decode_l3_fast(h, t1, t2, Eg, m);
         return decode_l3(h, t1, t2, Eg, m);
     }
 }
@@ -263,17 +264,18 @@ __device__ __forceinline__ double spmv_rows_block(const MatView& m, const double
         const int32_t* scol = reinterpret_cast<const int32_t*>(st);
         const int ls = (int)(rs - rb.e_lo), lt = (int)(rt - rb.e_lo);
         const int goff = (int)((rb.e_lo >> m.g_shift) - rb.g_lo);
-        int li = ls;
-        for (; li + 4 <= lt; li += 4) {
-            double xv[4], av[4];
+        // the row in batches of 8: all x gathers of a batch are in flight
+        // together (one round trip per batch), then the values are rebuilt
+        // and accumulated in order
+        for (int li = ls; li < lt; li += 8) {
+            const int cnt = lt - li;
+            double xv[8];
 #pragma unroll
-            for (int u = 0; u < 4; u++) xv[u] = __ldg(x + scol[li + u]);
+            for (int u = 0; u < 8; u++) xv[u] = u < cnt ? __ldg(x + scol[li + u]) : 0.0;
 #pragma unroll
-            for (int u = 0; u < 4; u++) av[u] = row_value<K, R>(m, L, st, li + u, goff);
-#pragma unroll
-            for (int u = 0; u < 4; u++) acc = fma(av[u], xv[u], acc);
+            for (int u = 0; u < 8; u++)
+                if (u < cnt) acc = fma(row_value<K, R>(m, L, st, li + u, goff), xv[u], acc);
         }
-        for (; li < lt; li++) acc = fma(row_value<K, R>(m, L, st, li, goff), __ldg(x + scol[li]), acc);
         const int64_t r = sb * RB + warp * 32 + lane;
         if (r < n) {
             if (DOT) dot = fma(__ldg(e.p + r), acc, dot);
