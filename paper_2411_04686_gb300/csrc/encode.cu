@@ -441,9 +441,9 @@ static int encode_impl(const gse_csr* csr, int G, const int* seg_bits, int n_seg
     v.carry = (double*)h->buf_carry;
     v.part = (double*)h->buf_part;
     h->mean_row_len = n > 0 ? (double)nnz / (double)n : 0.0;
-    // schedule: short rows in every 32-row block -> one row per lane; otherwise
-    // the nonzero split, 2 units of 8 per lane (gse_autotune refines this)
-    h->schedule_auto = h->row_span256 <= GSE_ROW_SPAN_MAX && h->max_row_len <= 64 ? GSE_SCHEDULE_ROWS : 2;
+    // schedule: short rows in every 256-row block -> one row per lane; otherwise
+    // the nonzero split, one unit of 8 per lane, 8-warp CTAs (gse_autotune refines this)
+    h->schedule_auto = h->row_span256 <= GSE_ROW_SPAN_MAX && h->max_row_len <= 64 ? GSE_SCHEDULE_ROWS : 1;
     h->schedule_forced = 0;
     return GSE_OK;
 #undef ALLOC

@@ -8,21 +8,21 @@
 
 namespace gse {
 
-constexpr int SPMV_STAGES = 3;
 // warps per CTA on the nonzero split: 8 / UPL, so a stage always holds 2048 nonzeros
 template <int UPL>
 constexpr int spmv_warps() { return 8 / UPL; }
 
 // y = A_k x (or b - A_k x) on the nonzero split: CTAs of 8/UPL warps walk
-// super-chunks of that many chunks through a TMA-filled stage ring.
-template <int K, int R, int UPL, bool RESID>
+// super-chunks of that many chunks through a TMA-filled ring of 2 or 3 stages
+// (whichever keeps more warps resident).
+template <int K, int R, int UPL, bool RESID, int STAGES>
 __global__ void __launch_bounds__(spmv_warps<UPL>() * 32) k_spmv(MatView m, const double* __restrict__ x, Epi e,
                                                                   int64_t n_chunks, ChunkStage L, int* err,
                                                                   const int* gate) {
     if (gate && *gate) return;
     extern __shared__ __align__(128) unsigned char smem[];
     fill_empty_rows(m, e, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
-    spmv_chunks_block<K, R, UPL, false, RESID, SPMV_STAGES>(m, x, e, blockIdx.x, gridDim.x, n_chunks, L, smem, err);
+    spmv_chunks_block<K, R, UPL, false, RESID, STAGES>(m, x, e, blockIdx.x, gridDim.x, n_chunks, L, smem, err);
 }
 
 // Finishes the rows that cross chunk boundaries (after k_spmv, same stream).
@@ -127,14 +127,22 @@ struct KernelPick {
     int warps;
 };
 
-template <int K, int R, int UPL, bool RESID>
-KernelPick pick_one(int r_lo) {
+template <int K, int R, int UPL, bool RESID, int STAGES>
+KernelPick pick_stages(int r_lo) {
     KernelPick kp;
-    kp.fn = k_spmv<K, R, UPL, RESID>;
+    kp.fn = k_spmv<K, R, UPL, RESID, STAGES>;
     kp.warps = spmv_warps<UPL>();
     kp.L = chunk_stage_layout<K, R, UPL>(kp.warps, r_lo);
-    kp.smem = (size_t)chunks_block_smem<SPMV_STAGES, UPL>(kp.L);
+    kp.smem = (size_t)chunks_block_smem<STAGES, UPL>(kp.L);
     return kp;
+}
+
+static int resident_blocks(const KernelPick& kp);
+
+template <int K, int R, int UPL, bool RESID>
+KernelPick pick_one(int r_lo) {
+    const KernelPick a = pick_stages<K, R, UPL, RESID, 3>(r_lo), b = pick_stages<K, R, UPL, RESID, 2>(r_lo);
+    return resident_blocks(b) > resident_blocks(a) ? b : a;
 }
 
 template <int K, int R, bool RESID>

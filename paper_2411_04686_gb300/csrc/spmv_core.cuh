@@ -11,8 +11,8 @@
 // stitched by a segmented warp scan of the lane carries (skipped when every lane
 // sees a row end, which holds whenever rows are at most 8 long); a row that
 // crosses chunks leaves one piece per chunk in scratch and is summed, in chunk
-// order, by fix_split_rows after the SpMV (deterministic).  Finished rows are
-// staged in shared memory and written back coalesced, through an epilogue.
+// order, by fix_split_rows after the SpMV (deterministic).  Finished rows go
+// through an epilogue from the lane that finishes them.
 #pragma once
 
 #include "gse_internal.cuh"

@@ -427,10 +427,15 @@ __device__ __forceinline__ void unit_values_blk(const MatView& m, const ChunkSta
 }
 
 // One warp's chunk c from a block-level stage (its units start at ub).
+// Every finished row goes straight through the epilogue from the lane that
+// finishes it: rows ending inside a lane after its first row end as soon as
+// they end, the lane's first row end once the segmented scan has supplied the
+// carries of the lanes before it.  No shared staging of row results, so a CTA
+// needs only its stage ring.
 template <int K, int R, int UPL, bool DOT, bool RESID>
 __device__ __forceinline__ double compute_chunk_blk(const MatView& m, const Epi& e, int64_t c, const ChunkStage& L,
                                                     const unsigned char* stage, int ub, const double* __restrict__ x,
-                                                    ChunkScalars sc, double* yb) {
+                                                    ChunkScalars sc) {
     const unsigned FULL = 0xFFFFFFFFu;
     const int lane = threadIdx.x & 31;
     const uint32_t* re = reinterpret_cast<const uint32_t*>(stage + L.off_re) + (ub >> 2);
@@ -458,7 +463,7 @@ __device__ __forceinline__ double compute_chunk_blk(const MatView& m, const Epi&
     }
     const int excl = incl - cnt;
     const int total_ends = __shfl_sync(FULL, incl, 31);
-    double cur = 0.0, hp = 0.0;
+    double cur = 0.0, hp = 0.0, dot = 0.0;
     int j = 0;
 #pragma unroll
     for (int q = 0; q < UPL; q++) {
@@ -467,12 +472,15 @@ __device__ __forceinline__ double compute_chunk_blk(const MatView& m, const Epi&
 #pragma unroll
         for (int i = 0; i < 8; i++) {
             cur = fma(a[i], xv[8 * q + i], cur);
-            if ((bits >> (q * 8 + i)) & 1u) {
-                if (j == 0) hp = cur;
-                else yb[excl + j] = cur;
-                j++;
-                cur = 0.0;
+            const bool end = (bits >> (q * 8 + i)) & 1u;
+            if (end && j > 0) {     // a row that starts and ends in this lane: ordinal excl + j >= 1
+                const int64_t Rw = actual_row(m, sc.row0 + excl + j);
+                if (DOT) dot = fma(__ldg(e.p + Rw), cur, dot);
+                epi_finish_t<RESID>(e, Rw, cur);
             }
+            hp = end && j == 0 ? cur : hp;
+            j += end ? 1 : 0;
+            cur = end ? 0.0 : cur;
         }
     }
     const bool seen = j > 0;
@@ -496,18 +504,20 @@ __device__ __forceinline__ double compute_chunk_blk(const MatView& m, const Epi&
     }
     double in = __shfl_up_sync(FULL, out, 1);
     if (lane == 0) in = 0.0;
-    if (seen) yb[excl] = in + hp;
+    if (seen) {                     // the lane's first row end: ordinal excl
+        const double v = in + hp;
+        if (excl == 0 && sc.starts_mid) {
+            // the piece of a row begun in an earlier chunk (summed by the fix pass)
+            if (DOT) dot = fma(__ldg(e.p + actual_row(m, sc.row0)), v, dot);
+            m.part[c] = v;
+        } else {
+            const int64_t Rw = actual_row(m, sc.row0 + excl);
+            if (DOT) dot = fma(__ldg(e.p + Rw), v, dot);
+            epi_finish_t<RESID>(e, Rw, v);
+        }
+    }
     const double out31 = __shfl_sync(FULL, out, 31);
     const bool last_end = __shfl_sync(FULL, (bits >> (8 * UPL - 1)) & 1u, 31) != 0;
-    __syncwarp();
-    double dot = 0.0;
-    for (int idx = lane; idx < total_ends; idx += 32) {
-        if (idx == 0 && sc.starts_mid) continue;
-        const int64_t Rw = actual_row(m, sc.row0 + idx);
-        const double v = yb[idx];
-        if (DOT) dot = fma(__ldg(e.p + Rw), v, dot);
-        epi_finish_t<RESID>(e, Rw, v);
-    }
     if (lane == 0) {
         if (total_ends == 0) {
             if (sc.row0 < m.n_nonempty) {
@@ -516,10 +526,6 @@ __device__ __forceinline__ double compute_chunk_blk(const MatView& m, const Epi&
                 else m.carry[c] = out31;
             }
         } else {
-            if (sc.starts_mid) {
-                if (DOT) dot = fma(__ldg(e.p + actual_row(m, sc.row0)), yb[0], dot);
-                m.part[c] = yb[0];
-            }
             const int64_t ro = sc.row0 + total_ends;
             if (!last_end && ro < m.n_nonempty) {
                 if (DOT) dot = fma(__ldg(e.p + actual_row(m, ro)), out31, dot);
@@ -527,13 +533,12 @@ __device__ __forceinline__ double compute_chunk_blk(const MatView& m, const Epi&
             }
         }
     }
-    __syncwarp();
     return dot;
 }
 
 // The CTA's share of an SpMV on the nonzero split: super-chunks sc0, sc0 +
-// scstride, ... of W chunks each (nch_total chunks in all).  smem: STAGES
-// stages, then W row-staging buffers of 256*UPL doubles.
+// scstride, ... of W chunks each (nch_total chunks in all).  smem: the STAGES
+// stages.
 template <int K, int R, int UPL, bool DOT, bool RESID, int STAGES>
 __device__ __forceinline__ double spmv_chunks_block(const MatView& m, const double* __restrict__ x, const Epi& e,
                                                     int64_t sc0, int64_t scstride, int64_t nch_total,
@@ -544,7 +549,6 @@ __device__ __forceinline__ double spmv_chunks_block(const MatView& m, const doub
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);
     uint64_t* empty = full + STAGES;
     unsigned char* stages = smem + 128;
-    double* yb = reinterpret_cast<double*>(smem + 128 + STAGES * L.bytes) + warp * CH;
     const bool producer = threadIdx.x == 0;
     const int64_t nsc = (nch_total + W - 1) / W;
     double dot = 0.0;
@@ -580,7 +584,7 @@ __device__ __forceinline__ double spmv_chunks_block(const MatView& m, const doub
         if (!ok) break;
         fphase ^= 1u << s;
         if (c < nch_total)
-            dot += compute_chunk_blk<K, R, UPL, DOT, RESID>(m, e, c, L, stages + s * L.bytes, warp * 32 * UPL, x, scs, yb);
+            dot += compute_chunk_blk<K, R, UPL, DOT, RESID>(m, e, c, L, stages + s * L.bytes, warp * 32 * UPL, x, scs);
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(empty + s));
         const int64_t si = sc + (int64_t)STAGES * scstride;
@@ -599,7 +603,7 @@ __device__ __forceinline__ double spmv_chunks_block(const MatView& m, const doub
 
 template <int STAGES, int UPL>
 __host__ __device__ inline int chunks_block_smem(const ChunkStage& L) {
-    return 128 + STAGES * L.bytes + L.nch * 256 * UPL * 8;
+    return 128 + STAGES * L.bytes;
 }
 
 }  // namespace gse
