@@ -84,8 +84,9 @@ class Clocks:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.first = self.proc.stdout.readline()     # the sampler is running before the region starts
         except (OSError, FileNotFoundError):
             self.proc = None
         return self
@@ -93,7 +94,6 @@ class Clocks:
     def __exit__(self, *a):
         self.lines = []
         if self.proc:
-            time.sleep(0.3)
             self.proc.terminate()
             try:
                 out, _ = self.proc.communicate(timeout=5)
@@ -181,7 +181,7 @@ def cpu_baseline(mats):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gse")
     ap.add_argument("--no-solve", action="store_true", help="skip every solver section")
@@ -193,6 +193,9 @@ def main():
     ap.add_argument("--profile-spmv", nargs=2, metavar=("MATRIX", "K"), default=None,
                     help="no timing: encode MATRIX (laplace3d_128 | powerlaw_1m), run gse_spmv at level K "
                          "(1, 2, 3, 64 = FP64 CSR) three times and exit; the target for ncu captures")
+    ap.add_argument("--profile-cg", type=int, metavar="N", default=None,
+                    help="no timing: FP64 and stepped CG once each on the N^3 Laplacian with shift 1e-3 "
+                         "and exit; the target for ncu captures of the engine kernels")
     ap.add_argument("--serve-requests", type=int, default=1000)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -210,6 +213,19 @@ def main():
             M.spmv(k, x, y)
         torch.cuda.synchronize()
         print(json.dumps({"profiled": name, "k": k, "schedule": M.info().schedule, "nnz": A.nnz}))
+        return
+
+    if args.profile_cg:
+        A = synth.laplace3d(args.profile_cg, shift=1e-3)
+        M = gse.GseMatrix.from_csr(A, attach=(64,))
+        b = torch.from_numpy(synth.rhs_ones(A)).cuda()
+        out = {}
+        for name, pol in (("fp64", gse.fp64_policy(gse.SCALED_CG)), ("gse", gse.SCALED_CG)):
+            x = torch.zeros(A.n_rows, dtype=torch.float64, device="cuda")
+            info = M.cg(b, x, tol=1e-10, policy=pol)
+            out[name] = {"iters": info["iters"], "status": info["status"], "switch_iter": info["switch_iter"]}
+        torch.cuda.synchronize()
+        print(json.dumps({"profiled_cg": args.profile_cg, **out}))
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

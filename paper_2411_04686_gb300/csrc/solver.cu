@@ -22,6 +22,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "solver_internal.cuh"
@@ -391,7 +392,9 @@ __global__ void __launch_bounds__(256) k_cg_p3(const SysDesc* __restrict__ sys, 
     const int64_t i0 = (int64_t)lb * blockDim.x + threadIdx.x, di = (int64_t)nblk * blockDim.x;
     // ||x||^2 feeds only the floor rule (GSE_POLICY_FLOOR); FP64 issue is scarce
     const bool xn = (S.prm.flags & GSE_POLICY_FLOOR) != 0;
-    if (pa == PA_UPDATE) {
+    // the x and p updates, with the ||x||^2 sum only when XN (separate loops,
+    // so no predicated-off FP64 work is issued)
+    auto update = [&](auto XN) {
         int64_t i = i0;
         for (; i + 3 * di < n; i += 4 * di) {          // four elements' loads in flight
             double pv[4], xv[4], rv[4];
@@ -402,7 +405,7 @@ __global__ void __launch_bounds__(256) k_cg_p3(const SysDesc* __restrict__ sys, 
                 const double xi = fma(alpha, pv[u], xv[u]);
                 x[i + u * di] = xi;
                 p[i + u * di] = fma(beta, pv[u], rv[u]);
-                if (xn) acc = fma(xi, xi, acc);
+                if constexpr (decltype(XN)::value) acc = fma(xi, xi, acc);
             }
         }
         for (; i < n; i += di) {
@@ -410,14 +413,22 @@ __global__ void __launch_bounds__(256) k_cg_p3(const SysDesc* __restrict__ sys, 
             const double xi = fma(alpha, pi, x[i]);
             x[i] = xi;
             p[i] = fma(beta, pi, r[i]);
-            if (xn) acc = fma(xi, xi, acc);
+            if constexpr (decltype(XN)::value) acc = fma(xi, xi, acc);
         }
-    } else if (pa == PA_XONLY) {
+    };
+    auto xonly = [&](auto XN) {
         for (int64_t i = i0; i < n; i += di) {
             const double xi = fma(alpha, p[i], x[i]);
             x[i] = xi;
-            if (xn) acc = fma(xi, xi, acc);
+            if constexpr (decltype(XN)::value) acc = fma(xi, xi, acc);
         }
+    };
+    if (pa == PA_UPDATE) {
+        if (xn) update(std::true_type{});
+        else update(std::false_type{});
+    } else if (pa == PA_XONLY) {
+        if (xn) xonly(std::true_type{});
+        else xonly(std::false_type{});
     } else if (pa == PA_COPY_R) {
         for (int64_t i = i0; i < n; i += di) p[i] = r[i];
     } else if (pa == PA_COPY_Q) {
