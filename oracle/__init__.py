@@ -83,6 +83,9 @@ def lib():
         L = ctypes.CDLL(_LIB)
         L.orc_encode.argtypes = [_I64, _P, _I, _P, _I, _P, _P, _P, _P]
         L.orc_decode.argtypes = [_I64, _P, _P, _P, _P, _I, _P, _I, _I, _P]
+        L.orc_table_build.argtypes = [_I64, _P, _I, _P]
+        L.orc_table_encode.argtypes = [_I64, _P, _P, _I, _P, _I, _P, _P, _P, _P]
+        L.orc_table_decode.argtypes = [_I64, _P, _P, _P, _P, _P, _I, _P, _I, _I, _P]
         L.orc_spmv.argtypes = [_I64, _P, _P, _P, _P, _P]
         L.orc_spmv.restype = None
         L.orc_gse_spmv.argtypes = [_I64, _P, _P, _P, _P, _P, _P, _I, _P, _I, _I, _P, _P]
@@ -145,6 +148,53 @@ def levels(val, group_size=32, seg_bits=(16, 16, 20)):
     """FP64 values of A_1 .. A_nseg decoded from the oracle's own encoding."""
     enc = encode(val, group_size, seg_bits)
     return [decode(*enc, k, group_size, seg_bits) for k in range(1, len(seg_bits) + 1)]
+
+
+def table_build(val, num_exp):
+    """The global shared-exponent table (Sec. III-B): int16 entries, each a
+    most frequent exponent plus 1, with max(e) + 1 always present."""
+    val = _c(val, np.float64)
+    table = np.zeros(max(num_exp, 1), np.int16)
+    n = lib().orc_table_build(val.size, _ptr(val), num_exp, _ptr(table))
+    if n < 1:
+        raise ValueError(f"orc_table_build status {n}")
+    return table[:n].copy()
+
+
+def table_encode(val, table, seg_bits=(16, 16, 20)):
+    """Alg. 1 against the table: (head u16, tail1 u16, tail2 u32, idx u8)."""
+    val = _c(val, np.float64)
+    table = _c(table, np.int16)
+    nnz = val.size
+    sb, nseg = _segs(seg_bits)
+    head = np.zeros(nnz, np.uint16)
+    t1 = np.zeros(nnz, np.uint16)
+    t2 = np.zeros(nnz, np.uint32)
+    idx = np.zeros(nnz, np.uint8)
+    rc = lib().orc_table_encode(nnz, _ptr(val), _ptr(table), table.size, _ptr(sb), nseg, _ptr(head), _ptr(t1),
+                                _ptr(t2), _ptr(idx))
+    if rc != 0:
+        raise ValueError(f"orc_table_encode status {rc}")
+    return head, t1, t2, idx
+
+
+def table_decode(head, tail1, tail2, idx, table, k, seg_bits=(16, 16, 20)):
+    head, tail1 = _c(head, np.uint16), _c(tail1, np.uint16)
+    tail2, idx, table = _c(tail2, np.uint32), _c(idx, np.uint8), _c(table, np.int16)
+    sb, nseg = _segs(seg_bits)
+    out = np.zeros(head.size, np.float64)
+    rc = lib().orc_table_decode(head.size, _ptr(head), _ptr(tail1), _ptr(tail2), _ptr(idx), _ptr(table), table.size,
+                                _ptr(sb), nseg, k, _ptr(out))
+    if rc != 0:
+        raise ValueError(f"orc_table_decode status {rc}")
+    return out
+
+
+def table_levels(val, num_exp, seg_bits=(16, 16, 20)):
+    """(table, [A_1 .. A_nseg values]) of the table format."""
+    table = table_build(val, num_exp)
+    enc = table_encode(val, table, seg_bits)
+    return table, [table_decode(*enc, table, k, seg_bits) for k in range(1, len(seg_bits) + 1)]
 
 
 def spmv(row_ptr, col, a, x):

@@ -26,6 +26,12 @@
  * bits and level k carries W_k = W_1 + s2 + ... + s_k.  E_g is the biased
  * group exponent, d = E_g - e >= 1 the alignment distance of one value.
  *
+ * Table variant (the paper's default format): orc_table_* keep one table of
+ * numExp shared exponents for the whole matrix (Sec. III-B) and an exponent
+ * index per nonzero (Sec. III-C keeps it in the column index's top bits); a
+ * value whose exponent plus 1 is not in the table is denormalized against the
+ * nearest larger entry (Alg. 1).  The segment split is the same.
+ *
  * Parity status: every function here is pinned by the CPU test suite (closed
  * forms, an independent transcription of Alg. 1/Alg. 2, brute force, exact
  * rational sums, textbook invariants, dense LU).  Nothing is unpinned.
@@ -148,6 +154,118 @@ int orc_decode(int64_t nnz, const uint16_t* head, const uint16_t* tail1, const u
     for (int64_t i = 0; i < nnz; i++)
         out[i] = decode_one(head[i], k >= 2 ? tail1[i] : 0, k >= 3 ? tail2[i] : 0,
                             gexp[i / G], seg_bits, k);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Global shared-exponent table (the paper's default format): one table of   */
+/* numExp shared exponents for the whole matrix (Sec. III-B), the exponent   */
+/* index of each nonzero kept beside its column index (Sec. III-C).          */
+
+/*
+ * Sec. III-B, "Shared Exponents Extraction": count the nonzeros carrying each
+ * exponent, order the exponents by count (descending; equal counts: the larger
+ * exponent first), keep the first numExp and store each one plus 1 (Sec. III-B,
+ * "Denormalized Representation": the hidden one becomes explicit).  The same
+ * passage requires max(e) + 1 to be one of them; when the largest exponent did
+ * not make the cut it replaces the last kept entry.  Zeros and subnormals
+ * (e = 0) are not counted.  Returns the number of entries (at most numExp); a
+ * matrix without a normal value gets the single entry 0.  Returns -ORC_NONFINITE
+ * when a value is Inf or NaN, ORC_ERR_INVALID for bad arguments.
+ */
+int orc_table_build(int64_t nnz, const double* val, int num_exp, int16_t* table)
+{
+    if (num_exp < 1 || nnz < 0) return ORC_ERR_INVALID;
+    int64_t* count = calloc(2048, sizeof(int64_t));
+    int emax = 0;
+    for (int64_t i = 0; i < nnz; i++) {
+        int e = (int)((bits_of(val[i]) >> 52) & 0x7FF);
+        if (e == 0x7FF) { free(count); return -ORC_NONFINITE; }
+        if (e == 0) continue;
+        count[e]++;
+        if (e > emax) emax = e;
+    }
+    if (emax == 0) { table[0] = 0; free(count); return 1; }
+    int n = 0;
+    int taken[2048] = {0};
+    while (n < num_exp) {                 /* selection by (count desc, exponent desc) */
+        int best = -1;
+        for (int e = 2046; e >= 1; e--)
+            if (count[e] > 0 && !taken[e] && (best < 0 || count[e] > count[best])) best = e;
+        if (best < 0) break;
+        taken[best] = 1;
+        table[n++] = (int16_t)(best + 1);
+    }
+    if (!taken[emax]) table[n - 1] = (int16_t)(emax + 1);
+    free(count);
+    return n;
+}
+
+/* Alg. 1, the search for one value's shared exponent: the entry equal to
+ * e + 1 (then minDiff = 1), else the nearest entry above e (minDiff = entry - e,
+ * the smallest positive difference).  e = 0 (zero or subnormal) takes index 0;
+ * its mantissa is 0 anyway. */
+static void table_lookup(int e, const int16_t* table, int n_table, int* idx, int* d)
+{
+    *idx = 0;
+    *d = 1;
+    if (e == 0) return;
+    for (int k = 0; k < n_table; k++)
+        if (table[k] == e + 1) { *idx = k; *d = 1; return; }
+    int min_diff = 1 << 30;
+    for (int jj = 0; jj < n_table; jj++) {
+        int diff = table[jj] - e;
+        if (diff > 0 && diff < min_diff) { min_diff = diff; *idx = jj; }
+    }
+    *d = min_diff;
+}
+
+/* Alg. 1 for every nonzero against the table, then the segment split of
+ * Fig. 3: M = floor(|v| * 2^(W - (T - 1023))) with T = table[index], i.e. the
+ * 53-bit significand S shifted right by 52 + d - W (truncation, as Alg. 1;
+ * M = 0 once the explicit one is shifted out).  idx receives the index. */
+int orc_table_encode(int64_t nnz, const double* val, const int16_t* table, int n_table,
+                     const int* seg_bits, int nseg, uint16_t* head, uint16_t* tail1, uint32_t* tail2,
+                     uint8_t* idx)
+{
+    int W = total_width(seg_bits, nseg);
+    if (W < 0 || n_table < 1 || nnz < 0) return ORC_ERR_INVALID;
+    int W1 = level_width(seg_bits, 1);
+    int W2 = nseg >= 2 ? level_width(seg_bits, 2) : W1;
+    for (int64_t i = 0; i < nnz; i++) {
+        uint64_t b = bits_of(val[i]);
+        uint64_t sign = b >> 63;
+        int e = (int)((b >> 52) & 0x7FF);
+        if (e == 0x7FF) return ORC_NONFINITE;
+        int k, d;
+        table_lookup(e, table, n_table, &k, &d);
+        uint64_t M = 0;
+        if (e != 0) {
+            uint64_t S = (1ULL << 52) | (b & ((1ULL << 52) - 1));
+            int shift = W - 52 - d;
+            if (shift >= 0) M = S << shift;
+            else if (-shift < 64) M = S >> (-shift);
+            else M = 0;
+        }
+        idx[i] = (uint8_t)k;
+        head[i] = (uint16_t)((sign << (seg_bits[0] - 1)) | (M >> (W - W1)));
+        if (tail1) tail1[i] = nseg >= 2 ? (uint16_t)((M >> (W - W2)) & ((1ULL << seg_bits[1]) - 1)) : 0;
+        if (tail2) tail2[i] = nseg >= 3 ? (uint32_t)(M & ((1ULL << seg_bits[2]) - 1)) : 0;
+    }
+    return ORC_OK;
+}
+
+/* Decode at level k with the table: as decode_one, the shared exponent being
+ * table[idx[i]] (Alg. 2 reads it from the exponent array by the index). */
+int orc_table_decode(int64_t nnz, const uint16_t* head, const uint16_t* tail1, const uint32_t* tail2,
+                     const uint8_t* idx, const int16_t* table, int n_table, const int* seg_bits, int nseg,
+                     int k, double* out)
+{
+    if (total_width(seg_bits, nseg) < 0 || k < 1 || k > nseg || n_table < 1) return ORC_ERR_INVALID;
+    for (int64_t i = 0; i < nnz; i++) {
+        if (idx[i] >= n_table) return ORC_ERR_INVALID;
+        out[i] = decode_one(head[i], k >= 2 ? tail1[i] : 0, k >= 3 ? tail2[i] : 0, table[idx[i]], seg_bits, k);
+    }
     return ORC_OK;
 }
 
