@@ -50,8 +50,9 @@ DFMA_PEAK_PER_S = 0.59e12
 
 
 def algorithmic_bytes(nnz, n_rows, n_cols, k, seg=(16, 16, 20), G=32):
-    """col 4 B + live segments + group exponent per nonzero, row_ptr, x once, y once."""
-    return nnz * (4 + sum(seg[:k]) / 8.0 + 2.0 / G) + 4 * (n_rows + 1) + 8 * n_cols + 8 * n_rows
+    """col 4 B + live segments + group exponent per nonzero, row_ptr, x once, y once.
+    G = 0: the global-table format (no per-group exponents; the index rides in col)."""
+    return nnz * (4 + sum(seg[:k]) / 8.0 + (2.0 / G if G else 0.0)) + 4 * (n_rows + 1) + 8 * n_cols + 8 * n_rows
 
 
 def csr_bytes(nnz, n_rows, n_cols, vbytes):
@@ -189,6 +190,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-table", action="store_true", help="skip the global-table format section")
     ap.add_argument("--batch-systems", type=int, default=512)
     ap.add_argument("--profile-spmv", nargs=2, metavar=("MATRIX", "K"), default=None,
                     help="no timing: encode MATRIX (laplace3d_128 | powerlaw_1m), run gse_spmv at level K "
@@ -347,6 +349,37 @@ def main():
         gse_k1 = per_k[f"{name}_k1"]["us"]
         baselines[f"{name}_speedup_k1_vs_fp64"] = round(baselines[f"{name}_fp64"]["us"] / gse_k1, 3)
 
+    # the paper's default format: one global table of numExp shared exponents
+    # (Sec. III-B), the index in the column word (Sec. III-C); per-level times
+    # at numExp = 8 and the numExp sweep of Sec. IV-B (time and max |y - y_FP64|)
+    table = None
+    if not args.no_table:
+        table = {}
+        for name, A, M, x, y in handles:
+            y64 = M.spmv(gse.LEVEL_FP64, x).clone()
+            sweep = {}
+            for ne in (2, 4, 8, 16, 32, 64):
+                T = gse.GseMatrix.from_csr(A, num_exp=ne)
+                row = {"entries": T.info().num_exp}
+                for k in ((1, 2, 3) if ne == 8 else (1,)):
+                    ts = []
+                    for r in range(10):
+                        flush_l2(r)
+                        e0, e1 = ev[0]
+                        e0.record(stream)
+                        T.spmv(k, x, y)
+                        e1.record(stream)
+                        torch.cuda.synchronize()
+                        ts.append(e0.elapsed_time(e1))
+                    ms = statistics.median(ts)
+                    nb = algorithmic_bytes(A.nnz, A.n_rows, A.n_cols, k, G=0)
+                    row[f"k{k}_us"] = round(ms * 1e3, 2)
+                    row[f"k{k}_GB_s"] = round(nb / (ms * 1e-3) / 1e9, 1)
+                    row[f"k{k}_max_abs_err_vs_fp64"] = float((T.spmv(k, x) - y64).abs().max().item())
+                sweep[f"num_exp_{ne}"] = row
+                T.free()
+            table[name] = sweep
+
     # e2e: through the C ABI with host buffers, copies inside the timed region
     pinned_x = [torch.from_numpy(synth.uniform_x(h[1].n_cols, seed=0)).pin_memory() for h in handles]
     pinned_y = [torch.empty(h[1].n_rows, dtype=torch.float64).pin_memory() for h in handles]
@@ -391,7 +424,8 @@ def main():
                        "group_size": 32, "seg_bits": [16, 16, 20], "l2": "flushed before each SpMV (256 MiB write, then a 256 MiB read so no dirty line is written back inside the timed kernel)",
                        "parallelism": "replicas" if world > 1 else "single_gpu",
                        "wall_s_timed_region": round(wall, 3)},
-            "roofline": roofline, "per_k": per_k, "baselines": baselines, "solve": solve, "gmres": gmres,
+            "roofline": roofline, "per_k": per_k, "baselines": baselines, "table_format": table,
+            "solve": solve, "gmres": gmres,
             "batched": batched, "served": served,
             "e2e": e2e, "gpu_launches": len(launches) * args.steps, "clocks": clocks,
             "cpu_baseline": cpu,
@@ -425,10 +459,25 @@ def solver_comparison(gse, torch):
         out[name] = {"seconds": round(dt, 4), "iters": info["iters"], "status": info["status"],
                      "k_final": info["k_final"], "switch_iter": info["switch_iter"],
                      "rel_res_true": info["rel_res_true"], "max_abs_err_vs_ones": err}
-    f = out["fp64_csr_cg"]["seconds"]
-    for name in ("gse_stepped_cg_paper_policy", "gse_stepped_cg_floor_policy"):
-        out[name]["speedup_vs_fp64"] = round(f / out[name]["seconds"], 3)
     M.free()
+    # the same solve on the global-table format (numExp = 8, the paper's setting)
+    T = gse.GseMatrix.from_csr(A, num_exp=8)
+    x = torch.zeros(A.n_rows, dtype=torch.float64, device="cuda")
+    T.cg(b, x, tol=1e-10, policy=gse.SCALED_CG)
+    x.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    info = T.cg(b, x, tol=1e-10, policy=gse.SCALED_CG)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    out["gse_stepped_cg_table8"] = {"seconds": round(dt, 4), "iters": info["iters"], "status": info["status"],
+                                    "k_final": info["k_final"], "switch_iter": info["switch_iter"],
+                                    "rel_res_true": info["rel_res_true"],
+                                    "max_abs_err_vs_ones": float((x - 1.0).abs().max().item())}
+    T.free()
+    f = out["fp64_csr_cg"]["seconds"]
+    for name in ("gse_stepped_cg_paper_policy", "gse_stepped_cg_floor_policy", "gse_stepped_cg_table8"):
+        out[name]["speedup_vs_fp64"] = round(f / out[name]["seconds"], 3)
     return out
 
 

@@ -99,6 +99,8 @@ typedef struct {
     double mean_row_len;
     int schedule;                 /* 1, 2, 4 (nonzero split) or GSE_SCHEDULE_ROWS */
     int64_t bytes_level[3];       /* algorithmic bytes read+written by one SpMV   */
+    int num_exp;                  /* table format: shared exponents in the table;
+                                     0 for the per-group format                   */
 } gse_matrix_info;
 
 /* Error name for a status code (static string). */
@@ -213,8 +215,34 @@ int gse_cg_noalloc(gse_handle h, const double* b, double* x, double tol, const g
 
 /* Host copies of the logical segments (tests): head[nnz], tail1[nnz],
  * tail2[nnz] (the s3-bit field, widened to 32 bits), gexp[n_groups].  Any
- * pointer may be NULL to skip that array.  Synchronises the handle's stream. */
+ * pointer may be NULL to skip that array.  Synchronises the device.  gexp must
+ * be NULL for a table-format handle (GSE_ERR_INVALID otherwise). */
 int gse_export(gse_handle h, uint16_t* head, uint16_t* tail1, uint32_t* tail2, int16_t* gexp);
+
+/*
+ * The paper's default layout: ONE table of shared exponents for the whole
+ * matrix (Sec. III-B "Shared Exponents Extraction" and "Denormalized
+ * Representation", Alg. 1), the exponent index of each nonzero stored in the
+ * top bits of its column index (Sec. III-C, Alg. 2):
+ *   table = the num_exp most frequent biased exponents, each + 1, ordered by
+ *           count (equal counts: larger exponent first); max exponent + 1 is
+ *           always an entry (it replaces the last kept one if it missed the cut);
+ *   a value with exponent e uses the entry e + 1 when present (d = 1), else the
+ *           nearest larger entry T (d = T - e);
+ *   M = floor(|v| * 2^(W - (T - 1023))), split into head / tail1 / tail2 as in
+ *           gse_encode (zeros and subnormals: M = 0, index 0).
+ * num_exp in [1, 64].  The index takes ceil(log2(entries)) bits, so n_cols must
+ * not exceed 2^(32 - bits) (GSE_ERR_UNSUPPORTED).  Every other call (SpMV at
+ * any level, baselines, solvers, decode, footprint) accepts the handle.
+ * Errors as gse_encode.
+ */
+int gse_encode_table(const gse_csr* csr, int num_exp, const int* seg_bits, int n_seg, void* stream,
+                     gse_handle* out);
+
+/* Table-format handle (tests): the table (at most 64 int16 entries, host),
+ * its entry count, and the index of every nonzero (idx[nnz], host).  Any
+ * pointer may be NULL.  GSE_ERR_INVALID for a per-group handle. */
+int gse_export_table(gse_handle h, int16_t* table, int* n_table, uint8_t* idx);
 
 /* vals[nnz] (device) = the FP64 values of A_k in CSR order (tests). */
 int gse_decode(gse_handle h, int k, double* vals, void* stream);
@@ -223,9 +251,10 @@ int gse_decode(gse_handle h, int k, double* vals, void* stream);
 int gse_matrix_get_info(gse_handle h, gse_matrix_info* info);
 
 /* Force the SpMV schedule: 1, 2 or 4 = nonzero split, that many units of 8
- * consecutive nonzeros per lane; GSE_SCHEDULE_ROWS = one row per lane, 32
- * consecutive rows per warp (only for matrices whose 32-row blocks hold at most
- * 1024 nonzeros, else GSE_ERR_UNSUPPORTED); 0 restores the automatic choice. */
+ * consecutive nonzeros per lane (the table format always runs 1);
+ * GSE_SCHEDULE_ROWS = one row per lane, 256 consecutive rows per CTA (only for
+ * matrices whose 256-row blocks span at most 4096 nonzeros, else
+ * GSE_ERR_UNSUPPORTED); 0 restores the automatic choice. */
 #define GSE_SCHEDULE_ROWS 8
 int gse_set_schedule(gse_handle h, int schedule);
 

@@ -27,7 +27,7 @@ EXPORTS = ["gse_strerror", "gse_encode", "gse_attach_values", "gse_spmv", "gse_c
            "gse_batch_cg", "gse_engine_create", "gse_engine_submit", "gse_engine_run",
            "gse_engine_poll", "gse_engine_cancel", "gse_engine_destroy", "gse_export", "gse_decode",
            "gse_matrix_get_info", "gse_set_schedule", "gse_autotune", "gse_footprint",
-           "gse_solve_footprint", "gse_free"]
+           "gse_solve_footprint", "gse_free", "gse_encode_table", "gse_export_table"]
 
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -66,7 +66,7 @@ class MatrixInfo(ctypes.Structure):
     _fields_ = [("n_rows", _I64), ("n_cols", _I64), ("nnz", _I64), ("n_groups", _I64),
                 ("n_empty_rows", _I64), ("group_size", _I), ("n_seg", _I), ("seg_bits", _I * 3),
                 ("max_row_len", _I), ("mean_row_len", _D), ("schedule", _I),
-                ("bytes_level", _I64 * 3)]
+                ("bytes_level", _I64 * 3), ("num_exp", _I)]
 
 
 _lib = None
@@ -88,6 +88,8 @@ def lib():
     L.gse_strerror.restype = ctypes.c_char_p
     L.gse_strerror.argtypes = [_I]
     L.gse_encode.argtypes = [ctypes.POINTER(CSR), _I, _P, _I, _P, ctypes.POINTER(_P)]
+    L.gse_encode_table.argtypes = [ctypes.POINTER(CSR), _I, _P, _I, _P, ctypes.POINTER(_P)]
+    L.gse_export_table.argtypes = [_P, _P, _P, _P]
     L.gse_attach_values.argtypes = [_P, ctypes.POINTER(CSR), _I, _P]
     L.gse_spmv.argtypes = [_P, _I, _P, _P, _P]
     for f in (L.gse_cg, L.gse_cg_noalloc, L.gse_gmres):
@@ -177,7 +179,7 @@ class GseMatrix:
     """An encoded matrix on the current CUDA device (owns a gse_handle)."""
 
     def __init__(self, row_ptr, col, val, n_cols=None, group_size=32, seg_bits=(16, 16, 20),
-                 stream=None, attach=()):
+                 stream=None, attach=(), num_exp=0):
         import torch
         L = lib()
         self._keep = []
@@ -201,8 +203,13 @@ class GseMatrix:
         sb = (ctypes.c_int * 3)(*(list(seg_bits) + [0] * (3 - len(seg_bits))))
         h = ctypes.c_void_p()
         self.stream = _stream_ptr(stream)
-        _check(L.gse_encode(ctypes.byref(self.csr), group_size, ctypes.cast(sb, _P), len(seg_bits),
-                            self.stream, ctypes.byref(h)), "gse_encode")
+        if num_exp:      # the paper's global exponent table (Sec. III-B), index in the column word
+            _check(L.gse_encode_table(ctypes.byref(self.csr), num_exp, ctypes.cast(sb, _P), len(seg_bits),
+                                      self.stream, ctypes.byref(h)), "gse_encode_table")
+        else:
+            _check(L.gse_encode(ctypes.byref(self.csr), group_size, ctypes.cast(sb, _P), len(seg_bits),
+                                self.stream, ctypes.byref(h)), "gse_encode")
+        self.num_exp = num_exp
         self.h = h
         self.group_size = group_size
         self.seg_bits = tuple(seg_bits)
@@ -248,8 +255,17 @@ class GseMatrix:
         t2 = np.zeros(self.nnz, np.uint32)
         gexp = np.zeros((self.nnz + self.group_size - 1) // self.group_size, np.int16)
         _check(lib().gse_export(self.h, head.ctypes.data, t1.ctypes.data, t2.ctypes.data,
-                                gexp.ctypes.data), "gse_export")
+                                None if self.num_exp else gexp.ctypes.data), "gse_export")
         return head, t1, t2, gexp
+
+    def export_table(self):
+        """(table int16, idx uint8) of a table-format handle."""
+        table = np.zeros(64, np.int16)
+        n = ctypes.c_int(0)
+        idx = np.zeros(max(self.nnz, 1), np.uint8)
+        _check(lib().gse_export_table(self.h, table.ctypes.data, ctypes.byref(n), idx.ctypes.data),
+               "gse_export_table")
+        return table[: n.value].copy(), idx[: self.nnz]
 
     def set_schedule(self, upl: int):
         _check(lib().gse_set_schedule(self.h, upl), "gse_set_schedule")

@@ -1,6 +1,7 @@
 // encode.cu -- gse_encode (Sec. III-B, Alg. 1, Fig. 3) and the handle's life
 // cycle: validation, the group-shared-exponent encoder, row-end mask and chunk
 // metadata, row statistics, baseline values, export/decode, footprint.
+#include <algorithm>
 #include <cstdlib>
 #include <cstring>
 #include <vector>
@@ -78,6 +79,110 @@ __global__ void k_encode(const double* __restrict__ val, const int32_t* __restri
         if ((lane & (p.G - 1)) == 0) gexp[e / p.G] = (uint16_t)Eg;
         col[e] = real ? col_in[e] : 0;
     }
+}
+
+// ---- global exponent table (Sec. III-B "Shared Exponents Extraction") -------
+
+// Occurrences of every biased exponent among the values (counted per block in
+// shared memory, then added to the global histogram).
+__global__ void k_exp_hist(const double* __restrict__ val, int64_t nnz, unsigned long long* hist) {
+    __shared__ unsigned int h[2048];
+    for (int i = threadIdx.x; i < 2048; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&h[(unsigned)((uint64_t)__double_as_longlong(val[e]) >> 52) & 0x7FFu], 1u);
+    __syncthreads();
+    for (int i = threadIdx.x; i < 2048; i += blockDim.x)
+        if (h[i]) atomicAdd(hist + i, (unsigned long long)h[i]);
+}
+
+// Alg. 1 against the table through a per-exponent lookup: lut[e] = index | d << 8
+// (the entry equal to e + 1 with d = 1, else the nearest larger entry T with
+// d = T - e), then the segment split of k_encode.  The index is stored in the
+// top bits of the column word.
+__global__ void k_encode_table(const double* __restrict__ val, const int32_t* __restrict__ col_in, int64_t nnz,
+                               int64_t nnz_pad, EncParams p, const uint32_t* __restrict__ lut, int ei_shift,
+                               int32_t* col, uint16_t* head, uint16_t* tail1, uint16_t* t2hi, uint32_t* t2lo,
+                               int* err) {
+    const unsigned FULL = 0xFFFFFFFFu;
+    __shared__ uint32_t slut[2048];
+    for (int i = threadIdx.x; i < 2048; i += blockDim.x) slut[i] = lut[i];
+    __syncthreads();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz_pad; e += stride) {
+        const bool real = e < nnz;
+        const uint64_t b = real ? (uint64_t)__double_as_longlong(val[e]) : 0ull;
+        const int ex = (int)((b >> 52) & 0x7FF);
+        if (ex == 0x7FF) atomicOr(err, 2);
+        const uint32_t l = slut[ex];
+        const uint32_t idx = l & 0xFFu;
+        const int d = (int)(l >> 8);
+        uint64_t M = 0;
+        if (ex != 0 && ex != 0x7FF) {
+            const uint64_t S = (1ull << 52) | (b & 0xFFFFFFFFFFFFFull);
+            const int sh = p.W - 52 - d;
+            M = sh >= 0 ? (S << sh) : (-sh < 64 ? (S >> (-sh)) : 0ull);
+        }
+        const uint32_t sign = (uint32_t)(b >> 63);
+        head[e] = (uint16_t)((sign << (p.s1 - 1)) | (uint32_t)(M >> (p.W - p.W1)));
+        if (p.n_seg >= 2) tail1[e] = (uint16_t)((M >> (p.W - p.W2)) & ((1ull << p.s2) - 1));
+        if (p.n_seg >= 3) {
+            const uint32_t t2 = (uint32_t)(M & ((1ull << p.s3) - 1));
+            t2hi[e] = (uint16_t)(t2 >> p.r_lo);
+            if (p.r_lo > 0) {
+                const int i = (int)(e & 7);
+                const int bit = i * p.r_lo;
+                uint32_t w = (t2 & ((1u << p.r_lo) - 1u)) << (bit & 31);
+                const int lanes_per_word = 32 / p.r_lo;
+                for (int o = 1; o < lanes_per_word; o <<= 1) w |= __shfl_xor_sync(FULL, w, o);
+                if ((i % lanes_per_word) == 0)
+                    t2lo[(e >> 3) * (p.r_lo / 4) + (bit >> 5)] = w;
+            }
+        }
+        const uint32_t c = real ? (uint32_t)col_in[e] : 0u;
+        col[e] = (int32_t)(ei_shift < 32 ? (c | (idx << ei_shift)) : c);
+    }
+}
+
+// Host side of the table: the num_exp most frequent exponents (count
+// descending, then exponent descending), each + 1, with max + 1 forced in
+// place of the last kept entry when it did not make the cut; then the lookup
+// of every exponent's entry and distance.  Returns the number of entries.
+static int build_table(const unsigned long long* hist, int num_exp, int16_t* table, uint32_t* lut) {
+    int order[2047];
+    int n_distinct = 0, emax = 0;
+    for (int e = 2046; e >= 1; e--)
+        if (hist[e]) {
+            order[n_distinct++] = e;
+            if (e > emax) emax = e;
+        }
+    std::stable_sort(order, order + n_distinct, [&](int a, int b) { return hist[a] > hist[b]; });
+    int n = 0;
+    if (n_distinct == 0) {
+        table[n++] = 0;
+    } else {
+        bool has_max = false;
+        for (int i = 0; i < n_distinct && n < num_exp; i++) {
+            table[n++] = (int16_t)(order[i] + 1);
+            has_max = has_max || order[i] == emax;
+        }
+        if (!has_max) table[n - 1] = (int16_t)(emax + 1);
+    }
+    for (int e = 0; e < 2048; e++) {
+        uint32_t idx = 0, d = 1;
+        if (e != 0) {
+            int best = -1, bd = 1 << 30;
+            for (int k = 0; k < n; k++) {
+                const int diff = table[k] - e;
+                if (diff == 1) { best = k; bd = 1; break; }
+                if (diff > 0 && diff < bd) { bd = diff; best = k; }
+            }
+            if (best >= 0) { idx = (uint32_t)best; d = (uint32_t)bd; }
+            else { idx = 0; d = 2047; }   // above every entry: cannot occur (max + 1 is in the table)
+        }
+        lut[e] = idx | (d << 8);
+    }
+    return n;
 }
 
 // ---- structure metadata -----------------------------------------------------
@@ -237,7 +342,7 @@ static unsigned grid_for(int64_t n, int threads = 256) {
 static void free_all(gse_matrix* h) {
     void* bufs[] = {h->buf_col, h->buf_head, h->buf_tail1, h->buf_t2hi, h->buf_t2lo, h->buf_gexp,
                     h->buf_rowend, h->buf_blk_row0, h->buf_nzrow, h->buf_empty, h->buf_row_ptr,
-                    h->buf_val64, h->buf_val32, h->buf_carry, h->buf_part,
+                    h->buf_val64, h->buf_val32, h->buf_carry, h->buf_part, h->buf_etab,
                     h->red_partial, h->red_counter, h->red_result, h->d_err};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -279,7 +384,7 @@ static int dev_alloc(T** p, size_t count, size_t* acc) {
 }
 
 static int encode_impl(const gse_csr* csr, int G, const int* seg_bits, int n_seg, cudaStream_t s,
-                       gse_matrix* h) {
+                       gse_matrix* h, int num_exp = 0) {
     const int64_t n = csr->n_rows, nnz = csr->nnz;
     h->group_size = G;
     h->n_seg = n_seg;
@@ -373,10 +478,59 @@ static int encode_impl(const gse_csr* csr, int G, const int* seg_bits, int n_seg
             p.W1 = v.W1;
             p.W2 = v.W2;
             p.n_seg = n_seg;
-            k_encode<<<grid_for(npad), 256, 0, s>>>(val, d_colin, nnz, npad, p, (int32_t*)h->buf_col,
-                                                    (uint16_t*)h->buf_head, (uint16_t*)h->buf_tail1,
-                                                    (uint16_t*)h->buf_t2hi, (uint32_t*)h->buf_t2lo,
-                                                    (uint16_t*)h->buf_gexp, d_err);
+            v.tbl = 0;
+            v.ei_shift = 32;
+            v.col_mask = 0xFFFFFFFFu;
+            h->num_exp = 0;
+            if (num_exp > 0) {
+                // the table format: histogram on the device, table and lookup on the host
+                unsigned long long* d_hist = nullptr;
+                uint32_t* d_lut = nullptr;
+                if (dev_alloc(&d_hist, 2048, &tacc) != GSE_OK || dev_alloc(&d_lut, 2048, &tacc) != GSE_OK) {
+                    status = GSE_ERR_OOM;
+                } else {
+                    cudaMemsetAsync(d_hist, 0, 2048 * sizeof(unsigned long long), s);
+                    if (nnz > 0) k_exp_hist<<<h->num_sms * 4, 512, 0, s>>>(val, nnz, d_hist);
+                    std::vector<unsigned long long> hist(2048);
+                    cudaMemcpyAsync(hist.data(), d_hist, 2048 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+                    if (cudaStreamSynchronize(s) != cudaSuccess) status = GSE_ERR_CUDA;
+                    std::vector<uint32_t> lut(2048);
+                    int16_t table[64] = {0};
+                    const int nt = status == GSE_OK ? build_table(hist.data(), num_exp, table, lut.data()) : 1;
+                    int ei_bits = 0;
+                    while ((1 << ei_bits) < nt) ei_bits++;
+                    if (status == GSE_OK && ei_bits > 0 && v.n_cols > (int64_t)(0xFFFFFFFFu >> ei_bits) + 1)
+                        status = GSE_ERR_UNSUPPORTED;     // the column index needs the bits the exponent index takes
+                    int16_t* d_etab = nullptr;
+                    if (status == GSE_OK && dev_alloc(&d_etab, 64, &h->bytes_matrix) != GSE_OK) status = GSE_ERR_OOM;
+                    if (status == GSE_OK) {
+                        h->buf_etab = d_etab;
+                        cudaMemcpyAsync(d_etab, table, sizeof(table), cudaMemcpyHostToDevice, s);
+                        v.etab = d_etab;
+                        v.tbl = 1;
+                        v.ei_shift = 32 - ei_bits;
+                        v.col_mask = 0xFFFFFFFFu >> ei_bits;
+                        memcpy(h->etab_host, table, sizeof(table));
+                        h->num_exp = nt;
+                        cudaMemcpyAsync(d_lut, lut.data(), 2048 * sizeof(uint32_t), cudaMemcpyHostToDevice, s);
+                        cudaMemsetAsync(h->buf_gexp, 0, npad / G * sizeof(uint16_t), s);
+                        k_encode_table<<<grid_for(npad), 256, 0, s>>>(val, d_colin, nnz, npad, p, d_lut, v.ei_shift,
+                                                                      (int32_t*)h->buf_col, (uint16_t*)h->buf_head,
+                                                                      (uint16_t*)h->buf_tail1, (uint16_t*)h->buf_t2hi,
+                                                                      (uint32_t*)h->buf_t2lo, d_err);
+                        cudaStreamSynchronize(s);          // the lookup buffer is freed right below
+                    }
+                }
+                if (d_hist) cudaFree(d_hist);
+                if (d_lut) cudaFree(d_lut);
+            } else {
+                k_encode<<<grid_for(npad), 256, 0, s>>>(val, d_colin, nnz, npad, p, (int32_t*)h->buf_col,
+                                                        (uint16_t*)h->buf_head, (uint16_t*)h->buf_tail1,
+                                                        (uint16_t*)h->buf_t2hi, (uint32_t*)h->buf_t2lo,
+                                                        (uint16_t*)h->buf_gexp, d_err);
+            }
+        }
+        if (status == GSE_OK) {
             // row ends, empty rows
             cudaMemsetAsync(h->buf_rowend, 0, npad / 32 * sizeof(uint32_t), s);
             if (n > 0) k_rowend<<<grid_for(n), 256, 0, s>>>(rp, n, (uint32_t*)h->buf_rowend, d_flag, d_flag2);
@@ -449,8 +603,8 @@ static int encode_impl(const gse_csr* csr, int G, const int* seg_bits, int n_seg
 #undef ALLOC
 }
 
-extern "C" int gse_encode(const gse_csr* csr, int group_size, const int* seg_bits, int n_seg,
-                          void* stream, gse_handle* out) {
+static int encode_entry(const gse_csr* csr, int group_size, const int* seg_bits, int n_seg, void* stream,
+                        gse_handle* out, int num_exp) {
     if (!csr || !seg_bits || !out) return GSE_ERR_INVALID;
     *out = nullptr;
     if (csr->n_rows < 0 || csr->n_cols < 0 || csr->nnz < 0 || csr->nnz >= (1LL << 31) ||
@@ -471,13 +625,40 @@ extern "C" int gse_encode(const gse_csr* csr, int group_size, const int* seg_bit
     cudaGetDevice(&h->device);
     cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
     if (h->num_sms < 1) h->num_sms = 1;
-    const int rc = encode_impl(csr, group_size, seg_bits, n_seg, (cudaStream_t)stream, h);
+    const int rc = encode_impl(csr, group_size, seg_bits, n_seg, (cudaStream_t)stream, h, num_exp);
     if (rc != GSE_OK) {
         free_all(h);
         free(h);
         return rc;
     }
     *out = h;
+    return GSE_OK;
+}
+
+extern "C" int gse_encode(const gse_csr* csr, int group_size, const int* seg_bits, int n_seg,
+                          void* stream, gse_handle* out) {
+    return encode_entry(csr, group_size, seg_bits, n_seg, stream, out, 0);
+}
+
+extern "C" int gse_encode_table(const gse_csr* csr, int num_exp, const int* seg_bits, int n_seg, void* stream,
+                                gse_handle* out) {
+    if (num_exp < 1 || num_exp > 64) return GSE_ERR_INVALID;
+    // group_size only sizes the (unused) group-exponent array here
+    return encode_entry(csr, 32, seg_bits, n_seg, stream, out, num_exp);
+}
+
+extern "C" int gse_export_table(gse_handle h, int16_t* table, int* n_table, uint8_t* idx) {
+    if (!h || !h->v.tbl) return GSE_ERR_INVALID;
+    cudaDeviceSynchronize();
+    if (table) memcpy(table, h->etab_host, (size_t)h->num_exp * sizeof(int16_t));
+    if (n_table) *n_table = h->num_exp;
+    const int64_t nnz = h->v.nnz;
+    if (idx && nnz) {
+        std::vector<uint32_t> c(nnz);
+        GSE_CUDA_TRY(cudaMemcpy(c.data(), h->buf_col, nnz * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+        for (int64_t e = 0; e < nnz; e++)
+            idx[e] = h->v.ei_shift < 32 ? (uint8_t)(c[e] >> h->v.ei_shift) : 0;
+    }
     return GSE_OK;
 }
 
@@ -546,6 +727,7 @@ extern "C" int gse_export(gse_handle h, uint16_t* head, uint16_t* tail1, uint32_
         }
     }
     const int64_t ng = (nnz + h->group_size - 1) / h->group_size;
+    if (gexp && h->v.tbl) return GSE_ERR_INVALID;     // table format: gse_export_table
     if (gexp && ng) GSE_CUDA_TRY(cudaMemcpy(gexp, h->buf_gexp, ng * sizeof(int16_t), cudaMemcpyDeviceToHost));
     return GSE_OK;
 }
@@ -584,6 +766,7 @@ extern "C" int gse_matrix_get_info(gse_handle h, gse_matrix_info* info) {
     info->max_row_len = h->max_row_len;
     info->mean_row_len = h->mean_row_len;
     info->schedule = units_per_lane(h);
+    info->num_exp = h->num_exp;
     // algorithmic bytes: col + live segments + group exponent per nonzero,
     // row_ptr, x read once, y written once
     const double nnz = (double)h->v.nnz, n = (double)h->v.n_rows, nc = (double)h->v.n_cols;

@@ -9,6 +9,12 @@
 //   t2lo    u32[nnz_pad / 8 * r / 4]  low r = s3 - 16 bits, packed per unit of
 //                                     8 nonzeros (r in {4, 8, 16}), r bytes each
 //   gexp    u16[n_groups]             group exponent E_g = max e + 1 (0: all zero)
+//                                     (group format only)
+// Table format (gse_encode_table): one table etab[num_exp] of shared exponents
+// for the whole matrix (each a frequent exponent + 1, max + 1 among them); the
+// index of a nonzero's entry sits in the top ei_bits bits of its col word
+// (col = index << (32 - ei_bits) | column), so every kernel masks col with
+// col_mask (all ones in the group format) and reads E = etab[col >> ei_shift].
 //   rowend  u32[nnz_pad / 32]         bit e: nonzero e is the last of its row
 //   blk_row0 int32[nnz_pad / 256]     compact index (nonempty rows only) of the
 //                                     row holding nonzero 256*b
@@ -52,7 +58,18 @@ struct MatView {
     int g_shift;               // log2(group size)
     int s1, s2, s3, s3hi, r_lo; // segment widths; s3hi = min(s3,16), r_lo = s3 - s3hi
     int W1, W2, W3;
+    int tbl;                   // 1: global exponent table (etab, index in col); 0: per-group gexp
+    int ei_shift;              // 32 - ei_bits (table format); the index is col >> ei_shift
+    uint32_t col_mask;         // column = col & col_mask
+    const int16_t* etab;       // the shared exponents (table format; device, 64 entries)
 };
+
+// Column index of a stored col word (strips the exponent index of the table format).
+__device__ __forceinline__ int32_t col_of(const MatView& m, int32_t c) { return (int32_t)((uint32_t)c & m.col_mask); }
+// Exponent-table index of a stored col word (table format).
+__device__ __forceinline__ int etab_index(const MatView& m, int32_t c) {
+    return (int)((uint64_t)(uint32_t)c >> m.ei_shift);
+}
 
 struct Workspace;  // solver vectors, allocated on first solve (solver.cu)
 
@@ -69,6 +86,9 @@ struct gse_matrix {
     int row_span;        // max nonzeros of any 32-row block, widened to groups of 32
     int row_span128;     // ... of any 128-row block (engine: 4-warp CTAs)
     int row_span256;     // ... of any 256-row block (standalone SpMV: 8-warp CTAs)
+    int num_exp;         // table format: entries of the exponent table (0: group format)
+    int16_t etab_host[64]; // table format: host copy of the table
+    void* buf_etab;      // table format: the table on the device (64 entries)
     int schedule_forced; // 0: automatic
     int num_sms;
     int device;

@@ -77,6 +77,14 @@ __device__ __forceinline__ bool sys_grid_last(unsigned* counter, int nblk) {
 template <bool ITER>
 __device__ __forceinline__ double eng_pipe(int k, const MatView& m, const double* x, const Epi& e, int64_t sc0,
                                            int64_t scs, int64_t nch, unsigned char* smem, int* err) {
+    if (m.tbl) {                      // table format: the shared exponent comes with each col word
+        switch (k) {
+            case 1: return spmv_chunks_block<1, 0, 1, ITER, !ITER, ENG_STAGES, true>(m, x, e, sc0, scs, nch, chunk_stage_layout<1, 0, 1>(ENG_WARPS, m.r_lo), smem, err);
+            case 2: return spmv_chunks_block<2, 0, 1, ITER, !ITER, ENG_STAGES, true>(m, x, e, sc0, scs, nch, chunk_stage_layout<2, 0, 1>(ENG_WARPS, m.r_lo), smem, err);
+            case 3: return spmv_chunks_block<3, -1, 1, ITER, !ITER, ENG_STAGES, true>(m, x, e, sc0, scs, nch, chunk_stage_layout<3, -1, 1>(ENG_WARPS, m.r_lo), smem, err);
+            default: break;
+        }
+    }
     switch (k) {
         case 1: return spmv_chunks_block<1, 0, 1, ITER, !ITER, ENG_STAGES>(m, x, e, sc0, scs, nch, chunk_stage_layout<1, 0, 1>(ENG_WARPS, m.r_lo), smem, err);
         case 2: return spmv_chunks_block<2, 0, 1, ITER, !ITER, ENG_STAGES>(m, x, e, sc0, scs, nch, chunk_stage_layout<2, 0, 1>(ENG_WARPS, m.r_lo), smem, err);
@@ -89,6 +97,14 @@ __device__ __forceinline__ double eng_pipe(int k, const MatView& m, const double
 template <bool ITER>
 __device__ __forceinline__ double eng_rows(int k, const MatView& m, const double* x, const Epi& e, int64_t sb0,
                                            int64_t sbs, int64_t nsb, int span, unsigned char* smem, int* err) {
+    if (m.tbl) {                      // table format: the shared exponent comes with each col word
+        switch (k) {
+            case 1: return spmv_rows_block<1, 0, ITER, !ITER, ENG_ROW_STAGES, true>(m, x, e, sb0, sbs, nsb, row_stage_layout<1, 0>(span, m.r_lo), smem, err);
+            case 2: return spmv_rows_block<2, 0, ITER, !ITER, ENG_ROW_STAGES, true>(m, x, e, sb0, sbs, nsb, row_stage_layout<2, 0>(span, m.r_lo), smem, err);
+            case 3: return spmv_rows_block<3, -1, ITER, !ITER, ENG_ROW_STAGES, true>(m, x, e, sb0, sbs, nsb, row_stage_layout<3, -1>(span, m.r_lo), smem, err);
+            default: break;
+        }
+    }
     switch (k) {
         case 1: return spmv_rows_block<1, 0, ITER, !ITER, ENG_ROW_STAGES>(m, x, e, sb0, sbs, nsb, row_stage_layout<1, 0>(span, m.r_lo), smem, err);
         case 2: return spmv_rows_block<2, 0, ITER, !ITER, ENG_ROW_STAGES>(m, x, e, sb0, sbs, nsb, row_stage_layout<2, 0>(span, m.r_lo), smem, err);

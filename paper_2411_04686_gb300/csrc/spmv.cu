@@ -15,14 +15,14 @@ constexpr int spmv_warps() { return 8 / UPL; }
 // y = A_k x (or b - A_k x) on the nonzero split: CTAs of 8/UPL warps walk
 // super-chunks of that many chunks through a TMA-filled ring of 2 or 3 stages
 // (whichever keeps more warps resident).
-template <int K, int R, int UPL, bool RESID, int STAGES>
+template <int K, int R, int UPL, bool RESID, int STAGES, bool TBL = false>
 __global__ void __launch_bounds__(spmv_warps<UPL>() * 32) k_spmv(MatView m, const double* __restrict__ x, Epi e,
                                                                   int64_t n_chunks, ChunkStage L, int* err,
                                                                   const int* gate) {
     if (gate && *gate) return;
     extern __shared__ __align__(128) unsigned char smem[];
     fill_empty_rows(m, e, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
-    spmv_chunks_block<K, R, UPL, false, RESID, STAGES>(m, x, e, blockIdx.x, gridDim.x, n_chunks, L, smem, err);
+    spmv_chunks_block<K, R, UPL, false, RESID, STAGES, TBL>(m, x, e, blockIdx.x, gridDim.x, n_chunks, L, smem, err);
 }
 
 // Finishes the rows that cross chunk boundaries (after k_spmv, same stream).
@@ -39,23 +39,28 @@ __global__ void __launch_bounds__(256) k_spmv_fix(MatView m, Epi e, int64_t n_ch
 // and FP64 cap the CTAs an SM holds by shared memory).
 constexpr int ROWS_WARPS = 8;
 
-template <int K, int R, bool RESID, int STAGES>
+template <int K, int R, bool RESID, int STAGES, bool TBL = false>
 __global__ void __launch_bounds__(ROWS_WARPS * 32) k_spmv_rows(MatView m, const double* __restrict__ x, Epi e,
                                                                 int64_t nsb, RowStage L, int* err, const int* gate) {
     if (gate && *gate) return;
     extern __shared__ __align__(128) unsigned char smem[];
-    spmv_rows_block<K, R, false, RESID, STAGES>(m, x, e, blockIdx.x, gridDim.x, nsb, L, smem, err);
+    spmv_rows_block<K, R, false, RESID, STAGES, TBL>(m, x, e, blockIdx.x, gridDim.x, nsb, L, smem, err);
 }
 
 typedef void (*RowsKernel)(MatView, const double*, Epi, int64_t, RowStage, int*, const int*);
 
 template <bool RESID, int STAGES>
-static RowsKernel pick_rows_t(int k, int r_lo, RowStage* L, int span) {
+static RowsKernel pick_rows_t(int k, int r_lo, RowStage* L, int span, bool tbl) {
     switch (k) {
-        case 1: *L = row_stage_layout<1, 0>(span, r_lo); return k_spmv_rows<1, 0, RESID, STAGES>;
-        case 2: *L = row_stage_layout<2, 0>(span, r_lo); return k_spmv_rows<2, 0, RESID, STAGES>;
+        case 1:
+            *L = row_stage_layout<1, 0>(span, r_lo);
+            return tbl ? k_spmv_rows<1, 0, RESID, STAGES, true> : k_spmv_rows<1, 0, RESID, STAGES>;
+        case 2:
+            *L = row_stage_layout<2, 0>(span, r_lo);
+            return tbl ? k_spmv_rows<2, 0, RESID, STAGES, true> : k_spmv_rows<2, 0, RESID, STAGES>;
         case 3:
             *L = row_stage_layout<3, -1>(span, r_lo);
+            if (tbl) return r_lo == 4 ? k_spmv_rows<3, 4, RESID, STAGES, true> : k_spmv_rows<3, -1, RESID, STAGES, true>;
             if (r_lo == 4) return k_spmv_rows<3, 4, RESID, STAGES>;
             if (r_lo == 0) return k_spmv_rows<3, 0, RESID, STAGES>;
             return k_spmv_rows<3, -1, RESID, STAGES>;
@@ -93,10 +98,11 @@ static int rows_resident(RowsKernel fn, size_t smem) {
 static int launch_rows(gse_matrix* h, int k, int epi, const SpmvArgs& a, cudaStream_t s) {
     RowStage L2, L3;
     const bool resid = epi == EPI_RESID;
-    RowsKernel f3 = resid ? pick_rows_t<true, 3>(k, h->v.r_lo, &L3, h->row_span256)
-                          : pick_rows_t<false, 3>(k, h->v.r_lo, &L3, h->row_span256);
-    RowsKernel f2 = resid ? pick_rows_t<true, 2>(k, h->v.r_lo, &L2, h->row_span256)
-                          : pick_rows_t<false, 2>(k, h->v.r_lo, &L2, h->row_span256);
+    const bool tbl = h->v.tbl != 0;
+    RowsKernel f3 = resid ? pick_rows_t<true, 3>(k, h->v.r_lo, &L3, h->row_span256, tbl)
+                          : pick_rows_t<false, 3>(k, h->v.r_lo, &L3, h->row_span256, tbl);
+    RowsKernel f2 = resid ? pick_rows_t<true, 2>(k, h->v.r_lo, &L2, h->row_span256, tbl)
+                          : pick_rows_t<false, 2>(k, h->v.r_lo, &L2, h->row_span256, tbl);
     const size_t smem3 = (size_t)rows_block_smem<3>(L3), smem2 = (size_t)rows_block_smem<2>(L2);
     const int nb3 = rows_resident(f3, smem3), nb2 = rows_resident(f2, smem2);
     const bool two = nb2 > nb3;
@@ -127,10 +133,10 @@ struct KernelPick {
     int warps;
 };
 
-template <int K, int R, int UPL, bool RESID, int STAGES>
+template <int K, int R, int UPL, bool RESID, int STAGES, bool TBL = false>
 KernelPick pick_stages(int r_lo) {
     KernelPick kp;
-    kp.fn = k_spmv<K, R, UPL, RESID, STAGES>;
+    kp.fn = k_spmv<K, R, UPL, RESID, STAGES, TBL>;
     kp.warps = spmv_warps<UPL>();
     kp.L = chunk_stage_layout<K, R, UPL>(kp.warps, r_lo);
     kp.smem = (size_t)chunks_block_smem<STAGES, UPL>(kp.L);
@@ -139,9 +145,9 @@ KernelPick pick_stages(int r_lo) {
 
 static int resident_blocks(const KernelPick& kp);
 
-template <int K, int R, int UPL, bool RESID>
+template <int K, int R, int UPL, bool RESID, bool TBL = false>
 KernelPick pick_one(int r_lo) {
-    const KernelPick a = pick_stages<K, R, UPL, RESID, 3>(r_lo), b = pick_stages<K, R, UPL, RESID, 2>(r_lo);
+    const KernelPick a = pick_stages<K, R, UPL, RESID, 3, TBL>(r_lo), b = pick_stages<K, R, UPL, RESID, 2, TBL>(r_lo);
     return resident_blocks(b) > resident_blocks(a) ? b : a;
 }
 
@@ -151,6 +157,18 @@ KernelPick pick_upl(int upl, int r_lo) {
         case 1: return pick_one<K, R, 1, RESID>(r_lo);
         case 2: return pick_one<K, R, 2, RESID>(r_lo);
         default: return pick_one<K, R, 4, RESID>(r_lo);
+    }
+}
+
+// Table format: one unit per lane on the nonzero split (exponent per value).
+template <bool RESID>
+static KernelPick pick_kernel_tbl(int k, int r_lo) {
+    switch (k) {
+        case 1: return pick_one<1, 0, 1, RESID, true>(r_lo);
+        case 2: return pick_one<2, 0, 1, RESID, true>(r_lo);
+        case 3: return r_lo == 4 ? pick_one<3, 4, 1, RESID, true>(r_lo) : pick_one<3, -1, 1, RESID, true>(r_lo);
+        case SRC_FP32: return pick_one<SRC_FP32, 0, 1, RESID>(r_lo);
+        default: return pick_one<SRC_FP64, 0, 1, RESID>(r_lo);
     }
 }
 
@@ -171,7 +189,8 @@ static KernelPick pick_kernel_t(int k, int r_lo, int upl) {
     }
 }
 
-static KernelPick pick_kernel(int k, int r_lo, int upl, bool resid) {
+static KernelPick pick_kernel(int k, int r_lo, int upl, bool resid, bool tbl) {
+    if (tbl) return resid ? pick_kernel_tbl<true>(k, r_lo) : pick_kernel_tbl<false>(k, r_lo);
     return resid ? pick_kernel_t<true>(k, r_lo, upl) : pick_kernel_t<false>(k, r_lo, upl);
 }
 
@@ -199,9 +218,10 @@ static int resident_blocks(const KernelPick& kp) {
 }
 
 int launch_spmv(gse_matrix* h, int k, int epi, const SpmvArgs& a, cudaStream_t s, int upl_override) {
-    const int upl = upl_override ? upl_override : units_per_lane(h);
+    int upl = upl_override ? upl_override : units_per_lane(h);
     if (upl == GSE_SCHEDULE_ROWS) return launch_rows(h, k, epi, a, s);
-    const KernelPick kp = pick_kernel(k, h->v.r_lo, upl, epi == EPI_RESID);
+    if (h->v.tbl) upl = 1;                     // the table format runs one unit per lane
+    const KernelPick kp = pick_kernel(k, h->v.r_lo, upl, epi == EPI_RESID, h->v.tbl != 0);
     const int64_t ch = 256 * upl;
     const int64_t n_chunks = (h->v.nnz + ch - 1) / ch;
     const int64_t resident = (int64_t)h->num_sms * resident_blocks(kp);

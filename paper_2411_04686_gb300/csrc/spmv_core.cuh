@@ -147,7 +147,7 @@ __device__ __forceinline__ void load_unit(const MatView& m, int64_t u, int* col,
         a[0] = widen_f32(fa.x); a[1] = widen_f32(fa.y); a[2] = widen_f32(fa.z); a[3] = widen_f32(fa.w);
         a[4] = widen_f32(fb.x); a[5] = widen_f32(fb.y); a[6] = widen_f32(fb.z); a[7] = widen_f32(fb.w);
     } else {
-        const int Eg = __ldg(m.gexp + ((u * GSE_UNIT) >> m.g_shift));
+        const int Eg0 = m.tbl ? 0 : (int)__ldg(m.gexp + ((u * GSE_UNIT) >> m.g_shift));
         const uint4 hw = __ldcs(reinterpret_cast<const uint4*>(m.head) + u);
         uint4 t1w = make_uint4(0, 0, 0, 0), t2w = make_uint4(0, 0, 0, 0);
         uint32_t lo[4] = {0, 0, 0, 0};
@@ -166,6 +166,7 @@ __device__ __forceinline__ void load_unit(const MatView& m, int64_t u, int* col,
 #pragma unroll
         for (int i = 0; i < 8; i++) {
             const uint32_t h = u16_of(hw, i);
+            const int Eg = m.tbl ? (int)__ldg(m.etab + etab_index(m, col[i])) : Eg0;   // table format: per value
             if constexpr (K == 1) {
                 a[i] = decode_l1(h, Eg, m);
             } else if constexpr (K == 2) {

@@ -119,7 +119,7 @@ __device__ __forceinline__ RowBlock row_block(int64_t s, int64_t t, int g_shift)
     return rb;
 }
 
-template <int K, int R>
+template <int K, int R, bool TBL = false>
 __device__ __forceinline__ void issue_rows(const MatView& m, const RowStage& L, RowBlock rb, unsigned char* stage,
                                            uint32_t bar) {
     const uint32_t n = (uint32_t)(rb.e_hi - rb.e_lo);
@@ -134,7 +134,7 @@ __device__ __forceinline__ void issue_rows(const MatView& m, const RowStage& L, 
     if constexpr (K == SRC_FP64) vbytes = n * 8;
     else if constexpr (K == SRC_FP32) vbytes = n * 4;
     else vbytes = n * 2 * (K >= 3 ? 3 : K) + (K >= 3 ? n * r / 8 : 0);
-    const bool gse_src = K != SRC_FP64 && K != SRC_FP32;
+    const bool gse_src = K != SRC_FP64 && K != SRC_FP32 && !TBL;   // the table format has no group exponents
     mbar_expect_tx(bar, n * 4 + vbytes + (gse_src ? gx_bytes : 0));
     const uint32_t s = smem_u32(stage);
     bulk_g2s(s, m.col + rb.e_lo, n * 4, bar);
@@ -150,21 +150,23 @@ __device__ __forceinline__ void issue_rows(const MatView& m, const RowStage& L, 
             bulk_g2s(s + L.off_v + 2 * sp2, m.t2hi + rb.e_lo, n * 2, bar);
             if (r > 0) bulk_g2s(s + L.off_v + 3 * sp2, m.t2lo + rb.e_lo / 8 * r / 4, n * r / 8, bar);
         }
-        bulk_g2s(s + L.off_gx, m.gexp + rb.g_lo, gx_bytes, bar);
+        if constexpr (!TBL) bulk_g2s(s + L.off_gx, m.gexp + rb.g_lo, gx_bytes, bar);
     }
 }
 
 // Value of the stage's nonzero i (stage-local index; its group is
-// (i >> g_shift) + goff in the stage's exponent run).
-template <int K, int R>
+// (i >> g_shift) + goff in the stage's exponent run; in the table format the
+// shared exponent is etab[index in the col word cw]).
+template <int K, int R, bool TBL = false>
 __device__ __forceinline__ double row_value(const MatView& m, const RowStage& L, const unsigned char* stage, int i,
-                                            int goff) {
+                                            int goff, int32_t cw = 0, const int16_t* etab = nullptr) {
     if constexpr (K == SRC_FP64) {
         return reinterpret_cast<const double*>(stage + L.off_v)[i];
     } else if constexpr (K == SRC_FP32) {
         return widen_f32(reinterpret_cast<const uint32_t*>(stage + L.off_v)[i]);
     } else {
-        const int Eg = reinterpret_cast<const uint16_t*>(stage + L.off_gx)[(i >> m.g_shift) + goff];
+        const int Eg = TBL ? (int)etab[etab_index(m, cw)]
+                           : (int)reinterpret_cast<const uint16_t*>(stage + L.off_gx)[(i >> m.g_shift) + goff];
         const uint16_t* hv = reinterpret_cast<const uint16_t*>(stage + L.off_v);
         const uint32_t h = hv[i];
         if constexpr (K == 1) return decode_l1_f(h, Eg, (uint32_t)(Eg - m.W1 - 127) << 20, m);
@@ -199,10 +201,12 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-template <int K, int R, bool DOT, bool RESID, int STAGES>
+template <int K, int R, bool DOT, bool RESID, int STAGES, bool TBL = false>
 __device__ __forceinline__ double spmv_rows_block(const MatView& m, const double* __restrict__ x, const Epi& e,
                                                   int64_t sb0, int64_t sbstride, int64_t nsb, const RowStage& L,
                                                   unsigned char* smem, int* err) {
+    __shared__ int16_t etab[64];                                  // table format: the shared exponents
+    if (TBL && threadIdx.x < 64) etab[threadIdx.x] = __ldg(m.etab + threadIdx.x);
     const unsigned FULL = 0xFFFFFFFFu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
     const int RB = 32 * W;                                        // rows per super-block
@@ -234,7 +238,7 @@ __device__ __forceinline__ double spmv_rows_block(const MatView& m, const double
             if (sb >= nsb) break;
             int64_t bs, bt;
             bounds(sb, &bs, &bt);
-            issue_rows<K, R>(m, L, row_block(bs, bt, m.g_shift), stages + s * L.bytes, smem_u32(full + s));
+            issue_rows<K, R, TBL>(m, L, row_block(bs, bt, m.g_shift), stages + s * L.bytes, smem_u32(full + s));
         }
     }
     __syncthreads();
@@ -271,10 +275,11 @@ __device__ __forceinline__ double spmv_rows_block(const MatView& m, const double
             const int cnt = lt - li;
             double xv[8];
 #pragma unroll
-            for (int u = 0; u < 8; u++) xv[u] = u < cnt ? __ldg(x + scol[li + u]) : 0.0;
+            for (int u = 0; u < 8; u++) xv[u] = u < cnt ? __ldg(x + col_of(m, scol[li + u])) : 0.0;
 #pragma unroll
             for (int u = 0; u < 8; u++)
-                if (u < cnt) acc = fma(row_value<K, R>(m, L, st, li + u, goff), xv[u], acc);
+                if (u < cnt)
+                    acc = fma(row_value<K, R, TBL>(m, L, st, li + u, goff, TBL ? scol[li + u] : 0, etab), xv[u], acc);
         }
         const int64_t r = sb * RB + warp * 32 + lane;
         if (r < n) {
@@ -289,7 +294,7 @@ __device__ __forceinline__ double spmv_rows_block(const MatView& m, const double
             if (!freed) atomicOr(err, 1);
             else {
                 fence_proxy_async_smem();
-                issue_rows<K, R>(m, L, row_block(is, it, m.g_shift), stages + s * L.bytes, smem_u32(full + s));
+                issue_rows<K, R, TBL>(m, L, row_block(is, it, m.g_shift), stages + s * L.bytes, smem_u32(full + s));
             }
         }
         ephase ^= 1u << s;
@@ -340,7 +345,7 @@ __host__ __device__ inline ChunkStage chunk_stage_layout(int W, int r_lo) {
     return L;
 }
 
-template <int K, int R, int UPL>
+template <int K, int R, int UPL, bool TBL = false>
 __device__ __forceinline__ void issue_superchunk(const MatView& m, const ChunkStage& L, int64_t sc, int64_t nch_total,
                                                  unsigned char* stage, uint32_t bar) {
     // chunks sc*W .. min(sc*W + W, nch_total) - 1 (the tail super-chunk may be short)
@@ -353,7 +358,7 @@ __device__ __forceinline__ void issue_superchunk(const MatView& m, const ChunkSt
     if constexpr (K == SRC_FP64) vbytes = e * 8;
     else if constexpr (K == SRC_FP32) vbytes = e * 4;
     else vbytes = e * 2 * (K >= 3 ? 3 : K) + (K >= 3 ? e * r / 8 : 0);
-    const bool gse_src = K != SRC_FP64 && K != SRC_FP32;
+    const bool gse_src = K != SRC_FP64 && K != SRC_FP32 && !TBL;
     mbar_expect_tx(bar, e * 4 + vbytes + e / 8 + (gse_src ? gx_bytes : 0));
     const uint32_t s = smem_u32(stage);
     const uint32_t E = (uint32_t)(L.nch * L.ch);    // full-stage stride of the segment arrays
@@ -369,15 +374,17 @@ __device__ __forceinline__ void issue_superchunk(const MatView& m, const ChunkSt
             bulk_g2s(s + L.off_v + E * 4, m.t2hi + e0, e * 2, bar);
             if (r > 0) bulk_g2s(s + L.off_v + E * 6, m.t2lo + e0 / 8 * r / 4, e * r / 8, bar);
         }
-        bulk_g2s(s + L.off_gx, m.gexp + (e0 >> m.g_shift), gx_bytes, bar);
+        if constexpr (!TBL) bulk_g2s(s + L.off_gx, m.gexp + (e0 >> m.g_shift), gx_bytes, bar);
     }
     bulk_g2s(s + L.off_re, m.rowend + e0 / 32, e / 8, bar);
 }
 
-// Values of unit u (stage-relative unit index) of a block-level stage.
-template <int K, int R>
+// Values of unit u (stage-relative unit index) of a block-level stage; in the
+// table format each value's shared exponent comes from its col word cw[i].
+template <int K, int R, bool TBL = false>
 __device__ __forceinline__ void unit_values_blk(const MatView& m, const ChunkStage& L, const unsigned char* stage,
-                                                int u, double* a) {
+                                                int u, double* a, const int32_t* cw = nullptr,
+                                                const int16_t* etab = nullptr) {
     const int E = L.nch * L.ch;
     if constexpr (K == SRC_FP64) {
         const double2* v2 = reinterpret_cast<const double2*>(stage + L.off_v) + 4 * u;
@@ -394,7 +401,7 @@ __device__ __forceinline__ void unit_values_blk(const MatView& m, const ChunkSta
         a[4] = widen_f32(fb.x); a[5] = widen_f32(fb.y); a[6] = widen_f32(fb.z); a[7] = widen_f32(fb.w);
     } else {
         const uint16_t* gx = reinterpret_cast<const uint16_t*>(stage + L.off_gx);
-        const int Eg = gx[(u * GSE_UNIT) >> m.g_shift];
+        const int Eg0 = TBL ? 0 : (int)gx[(u * GSE_UNIT) >> m.g_shift];
         const uint4 hw = reinterpret_cast<const uint4*>(stage + L.off_v)[u];
         uint4 t1w = make_uint4(0, 0, 0, 0), t2w = make_uint4(0, 0, 0, 0);
         uint32_t lo[4] = {0, 0, 0, 0};
@@ -410,6 +417,7 @@ __device__ __forceinline__ void unit_values_blk(const MatView& m, const ChunkSta
 #pragma unroll
         for (int i = 0; i < 8; i++) {
             const uint32_t h = u16_of(hw, i);
+            const int Eg = TBL ? (int)etab[etab_index(m, cw[i])] : Eg0;
             if constexpr (K == 1) {
                 a[i] = decode_l1_f(h, Eg, (uint32_t)(Eg - m.W1 - 127) << 20, m);
             } else if constexpr (K == 2) {
@@ -432,10 +440,10 @@ __device__ __forceinline__ void unit_values_blk(const MatView& m, const ChunkSta
 // they end, the lane's first row end once the segmented scan has supplied the
 // carries of the lanes before it.  No shared staging of row results, so a CTA
 // needs only its stage ring.
-template <int K, int R, int UPL, bool DOT, bool RESID>
+template <int K, int R, int UPL, bool DOT, bool RESID, bool TBL = false>
 __device__ __forceinline__ double compute_chunk_blk(const MatView& m, const Epi& e, int64_t c, const ChunkStage& L,
                                                     const unsigned char* stage, int ub, const double* __restrict__ x,
-                                                    ChunkScalars sc) {
+                                                    ChunkScalars sc, const int16_t* etab = nullptr) {
     const unsigned FULL = 0xFFFFFFFFu;
     const int lane = threadIdx.x & 31;
     const uint32_t* re = reinterpret_cast<const uint32_t*>(stage + L.off_re) + (ub >> 2);
@@ -445,14 +453,19 @@ __device__ __forceinline__ double compute_chunk_blk(const MatView& m, const Epi&
     else bits = (re[lane >> 2] >> ((lane & 3) * 8)) & 0xFFu;
     // x gathers for the lane's 8*UPL nonzeros, issued before the scans
     double xv[8 * UPL];
+    int32_t cw[TBL ? 8 * UPL : 1];
     const int4* c4 = reinterpret_cast<const int4*>(stage) + 2 * (ub + UPL * lane);
 #pragma unroll
     for (int q = 0; q < UPL; q++) {
         const int4 ca = c4[2 * q], cb = c4[2 * q + 1];
-        xv[8 * q + 0] = __ldg(x + ca.x); xv[8 * q + 1] = __ldg(x + ca.y);
-        xv[8 * q + 2] = __ldg(x + ca.z); xv[8 * q + 3] = __ldg(x + ca.w);
-        xv[8 * q + 4] = __ldg(x + cb.x); xv[8 * q + 5] = __ldg(x + cb.y);
-        xv[8 * q + 6] = __ldg(x + cb.z); xv[8 * q + 7] = __ldg(x + cb.w);
+        xv[8 * q + 0] = __ldg(x + col_of(m, ca.x)); xv[8 * q + 1] = __ldg(x + col_of(m, ca.y));
+        xv[8 * q + 2] = __ldg(x + col_of(m, ca.z)); xv[8 * q + 3] = __ldg(x + col_of(m, ca.w));
+        xv[8 * q + 4] = __ldg(x + col_of(m, cb.x)); xv[8 * q + 5] = __ldg(x + col_of(m, cb.y));
+        xv[8 * q + 6] = __ldg(x + col_of(m, cb.z)); xv[8 * q + 7] = __ldg(x + col_of(m, cb.w));
+        if constexpr (TBL) {
+            cw[8 * q + 0] = ca.x; cw[8 * q + 1] = ca.y; cw[8 * q + 2] = ca.z; cw[8 * q + 3] = ca.w;
+            cw[8 * q + 4] = cb.x; cw[8 * q + 5] = cb.y; cw[8 * q + 6] = cb.z; cw[8 * q + 7] = cb.w;
+        }
     }
     const int cnt = __popc(bits);
     int incl = cnt;
@@ -468,7 +481,7 @@ __device__ __forceinline__ double compute_chunk_blk(const MatView& m, const Epi&
 #pragma unroll
     for (int q = 0; q < UPL; q++) {
         double a[8];
-        unit_values_blk<K, R>(m, L, stage, ub + lane * UPL + q, a);
+        unit_values_blk<K, R, TBL>(m, L, stage, ub + lane * UPL + q, a, TBL ? cw + 8 * q : nullptr, etab);
 #pragma unroll
         for (int i = 0; i < 8; i++) {
             cur = fma(a[i], xv[8 * q + i], cur);
@@ -539,10 +552,12 @@ __device__ __forceinline__ double compute_chunk_blk(const MatView& m, const Epi&
 // The CTA's share of an SpMV on the nonzero split: super-chunks sc0, sc0 +
 // scstride, ... of W chunks each (nch_total chunks in all).  smem: the STAGES
 // stages.
-template <int K, int R, int UPL, bool DOT, bool RESID, int STAGES>
+template <int K, int R, int UPL, bool DOT, bool RESID, int STAGES, bool TBL = false>
 __device__ __forceinline__ double spmv_chunks_block(const MatView& m, const double* __restrict__ x, const Epi& e,
                                                     int64_t sc0, int64_t scstride, int64_t nch_total,
                                                     const ChunkStage& L, unsigned char* smem, int* err) {
+    __shared__ int16_t etab[64];                                  // table format: the shared exponents
+    if (TBL && threadIdx.x < 64) etab[threadIdx.x] = __ldg(m.etab + threadIdx.x);
     const unsigned FULL = 0xFFFFFFFFu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = L.nch;
     constexpr int CH = 256 * UPL;
@@ -562,7 +577,7 @@ __device__ __forceinline__ double spmv_chunks_block(const MatView& m, const doub
         for (int s = 0; s < STAGES; s++) {
             const int64_t sc = sc0 + s * scstride;
             if (sc >= nsc) break;
-            issue_superchunk<K, R, UPL>(m, L, sc, nch_total, stages + s * L.bytes, smem_u32(full + s));
+            issue_superchunk<K, R, UPL, TBL>(m, L, sc, nch_total, stages + s * L.bytes, smem_u32(full + s));
         }
     }
     __syncthreads();
@@ -584,7 +599,8 @@ __device__ __forceinline__ double spmv_chunks_block(const MatView& m, const doub
         if (!ok) break;
         fphase ^= 1u << s;
         if (c < nch_total)
-            dot += compute_chunk_blk<K, R, UPL, DOT, RESID>(m, e, c, L, stages + s * L.bytes, warp * 32 * UPL, x, scs);
+            dot += compute_chunk_blk<K, R, UPL, DOT, RESID, TBL>(m, e, c, L, stages + s * L.bytes, warp * 32 * UPL, x,
+                                                                 scs, etab);
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(empty + s));
         const int64_t si = sc + (int64_t)STAGES * scstride;
@@ -592,7 +608,7 @@ __device__ __forceinline__ double spmv_chunks_block(const MatView& m, const doub
             if (!mbar_wait_bounded(smem_u32(empty + s), (ephase >> s) & 1u)) atomicOr(err, 1);
             else {
                 fence_proxy_async_smem();
-                issue_superchunk<K, R, UPL>(m, L, si, nch_total, stages + s * L.bytes, smem_u32(full + s));
+                issue_superchunk<K, R, UPL, TBL>(m, L, si, nch_total, stages + s * L.bytes, smem_u32(full + s));
             }
         }
         ephase ^= 1u << s;

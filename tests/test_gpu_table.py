@@ -1,0 +1,125 @@
+"""The paper's global shared-exponent table format on the GPU vs the oracle
+(Sec. III-B "Shared Exponents Extraction", Alg. 1, Alg. 2, Sec. III-C):
+bit-exact table, indices and segments; bit-exact decode; SpMV within
+1e-13 * sum_j |a_ij x_j| of the oracle's Dot2 sum at every level and schedule;
+stepped CG on the table levels; the column-bit limit of the index."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import check_spmv_rows
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2411_04686_gb300 as gse  # noqa: E402
+
+SEG = (16, 16, 20)
+
+MATS = {
+    "poisson32_third": lambda: synth.poisson2d(32, 1.0 / 3.0),
+    "laplace3d_24": lambda: synth.laplace3d(24, shift=1e-3),
+    "powerlaw_50k": lambda: synth.powerlaw_random(50000, 16.0, 2048, seed=11),
+    "tiny": lambda: synth.CSR(np.array([0, 1, 3], np.int32), np.array([1, 0, 1], np.int32),
+                              np.array([2.5, -1.0, 1 / 3]), 2, "tiny"),
+}
+
+
+@pytest.mark.parametrize("name", list(MATS))
+@pytest.mark.parametrize("num_exp", [1, 2, 8, 64])
+def test_table_encode_bit_exact(name, num_exp):
+    A = MATS[name]()
+    M = gse.GseMatrix.from_csr(A, num_exp=num_exp)
+    table, idx = M.export_table()
+    ref_table = oracle.table_build(A.val, num_exp)
+    assert table.tolist() == ref_table.tolist()
+    rh, r1, r2, ridx = oracle.table_encode(A.val, ref_table, SEG)
+    assert np.array_equal(idx, ridx)
+    head, t1, t2, _ = M.export()
+    assert np.array_equal(head, rh) and np.array_equal(t1, r1) and np.array_equal(t2, r2)
+    assert M.info().num_exp == len(table)
+    for k in (1, 2, 3):
+        dec = M.decode(k).cpu().numpy()
+        ref = oracle.table_decode(rh, r1, r2, ridx, ref_table, k, SEG)
+        assert np.array_equal(dec.view(np.uint64), ref.view(np.uint64)), k
+
+
+@pytest.mark.parametrize("name", list(MATS))
+@pytest.mark.parametrize("sched", [1, gse.SCHEDULE_ROWS])
+def test_table_spmv_against_oracle(name, sched):
+    A = MATS[name]()
+    M = gse.GseMatrix.from_csr(A, num_exp=8, attach=(64,))
+    try:
+        M.set_schedule(sched)
+    except gse.GseError as e:          # row blocks too wide for the row schedule
+        assert e.code == gse.ERR_UNSUPPORTED and sched == gse.SCHEDULE_ROWS
+        return
+    x = synth.uniform_x(A.n_cols, seed=4)
+    xd = torch.from_numpy(x).cuda()
+    table, levels = oracle.table_levels(A.val, 8, SEG)
+    for k in (1, 2, 3):
+        y = M.spmv(k, xd).cpu().numpy()
+        check_spmv_rows(y, A, levels[k - 1], x)
+    # the FP64 baseline masks the exponent index out of the column words
+    y64 = M.spmv(gse.LEVEL_FP64, xd).cpu().numpy()
+    check_spmv_rows(y64, A, A.val, x)
+
+
+@pytest.mark.parametrize("name,sched", [("laplace3d_128", gse.SCHEDULE_ROWS), ("powerlaw_1m", 1)])
+def test_table_spmv_full_size_sampled(name, sched):
+    A = synth.laplace3d(128) if name == "laplace3d_128" else synth.powerlaw_random(1_000_000, 16.0, 2048, seed=0)
+    M = gse.GseMatrix.from_csr(A, num_exp=8)
+    M.set_schedule(sched)
+    x = synth.uniform_x(A.n_cols, seed=0)
+    xd = torch.from_numpy(x).cuda()
+    table, levels = oracle.table_levels(A.val, 8, SEG)
+    rows = np.random.default_rng(1).choice(A.n_rows, 3000, replace=False)
+    for k in (1, 2, 3):
+        y = M.spmv(k, xd).cpu().numpy()
+        check_spmv_rows(y, A, levels[k - 1], x, rows=rows)
+
+
+def test_table_stepped_cg_against_oracle():
+    A = synth.poisson2d(32, 1.0 / 3.0)
+    M = gse.GseMatrix.from_csr(A, num_exp=8)
+    b = synth.rhs_ones(A)
+    x = torch.zeros(A.n_rows, dtype=torch.float64, device="cuda")
+    info = M.cg(torch.from_numpy(b).cuda(), x, tol=1e-10, policy=gse.SCALED_CG)
+    _, levels = oracle.table_levels(A.val, 8, SEG)
+    ref = oracle.stepped_cg(A.row_ptr, A.col, levels, b, tol=1e-10, policy=oracle.SCALED_CG)
+    assert info["status"] == gse.OK and info["rel_res_true"] < 1e-10
+    assert info["k_final"] == ref["info"]["k_final"]
+    assert abs(info["iters"] - ref["info"]["iters"]) <= 3
+    assert np.max(np.abs(x.cpu().numpy() - ref["x"])) < 1e-8
+
+
+def test_table_gmres_runs():
+    A = synth.convdiff2d(32)
+    M = gse.GseMatrix.from_csr(A, num_exp=8)
+    b = synth.rhs_ones(A)
+    x = torch.zeros(A.n_rows, dtype=torch.float64, device="cuda")
+    info = M.gmres(torch.from_numpy(b).cuda(), x, tol=1e-10, policy=gse.SCALED_GMRES)
+    assert info["status"] == gse.OK and info["rel_res_true"] < 1e-10
+
+
+def test_table_index_needs_free_column_bits():
+    # 40 distinct exponents -> 6 index bits -> columns must stay below 2^26
+    vals = 2.0 ** np.arange(-20, 20, dtype=np.float64)
+    n_cols = 1 << 27
+    cols = np.sort(np.random.default_rng(2).choice(n_cols, vals.size, replace=False)).astype(np.int32)
+    cols[-1] = n_cols - 1
+    A = synth.CSR(np.array([0, vals.size], np.int32), cols, vals, n_cols, "wide")
+    with pytest.raises(gse.GseError) as e:
+        gse.GseMatrix.from_csr(A, num_exp=64)
+    assert e.value.code == gse.ERR_UNSUPPORTED
+    # with few entries the index fits
+    gse.GseMatrix.from_csr(A, num_exp=2)
+
+
+def test_table_rejects_bad_num_exp():
+    A = synth.poisson2d(8)
+    for ne in (-1, 65):
+        with pytest.raises(gse.GseError) as e:
+            gse.GseMatrix.from_csr(A, num_exp=ne)
+        assert e.value.code == gse.ERR_INVALID
