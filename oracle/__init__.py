@@ -84,6 +84,8 @@ def lib():
         L.orc_encode.argtypes = [_I64, _P, _I, _P, _I, _P, _P, _P, _P]
         L.orc_decode.argtypes = [_I64, _P, _P, _P, _P, _I, _P, _I, _I, _P]
         L.orc_table_build.argtypes = [_I64, _P, _I, _P]
+        L.orc_round16.argtypes = [_I64, _P, _I, _P, ctypes.POINTER(_I64)]
+        L.orc_widen16.argtypes = [_I64, _P, _I, _P]
         L.orc_table_encode.argtypes = [_I64, _P, _P, _I, _P, _I, _P, _P, _P, _P]
         L.orc_table_decode.argtypes = [_I64, _P, _P, _P, _P, _P, _I, _P, _I, _I, _P]
         L.orc_spmv.argtypes = [_I64, _P, _P, _P, _P, _P]
@@ -195,6 +197,30 @@ def table_levels(val, num_exp, seg_bits=(16, 16, 20)):
     table = table_build(val, num_exp)
     enc = table_encode(val, table, seg_bits)
     return table, [table_decode(*enc, table, k, seg_bits) for k in range(1, len(seg_bits) + 1)]
+
+
+FP16, BF16 = 16, 17
+
+
+def round16(val, kind):
+    """(bits uint16, n_overflow): FP16 (kind 16) or BF16 (kind 17) storage of
+    the values, round to nearest even from FP64 (Sec. IV-C baselines)."""
+    val = _c(val, np.float64)
+    out = np.zeros(val.size, np.uint16)
+    ov = _I64(0)
+    rc = lib().orc_round16(val.size, _ptr(val), kind, _ptr(out), ctypes.byref(ov))
+    if rc != 0:
+        raise ValueError(f"orc_round16 status {rc}")
+    return out, int(ov.value)
+
+
+def widen16(bits, kind):
+    bits = _c(bits, np.uint16)
+    out = np.zeros(bits.size, np.float64)
+    rc = lib().orc_widen16(bits.size, _ptr(bits), kind, _ptr(out))
+    if rc != 0:
+        raise ValueError(f"orc_widen16 status {rc}")
+    return out
 
 
 def spmv(row_ptr, col, a, x):

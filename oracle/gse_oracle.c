@@ -32,6 +32,10 @@
  * value whose exponent plus 1 is not in the table is denormalized against the
  * nearest larger entry (Alg. 1).  The segment split is the same.
  *
+ * 16-bit baselines: orc_round16 / orc_widen16 store the values as FP16 or
+ * BF16 (round to nearest even, one rounding from FP64) for the baseline SpMV
+ * and solvers of Sec. IV-C.
+ *
  * Parity status: every function here is pinned by the CPU test suite (closed
  * forms, an independent transcription of Alg. 1/Alg. 2, brute force, exact
  * rational sums, textbook invariants, dense LU).  Nothing is unpinned.
@@ -266,6 +270,71 @@ int orc_table_decode(int64_t nnz, const uint16_t* head, const uint16_t* tail1, c
         if (idx[i] >= n_table) return ORC_ERR_INVALID;
         out[i] = decode_one(head[i], k >= 2 ? tail1[i] : 0, k >= 3 ? tail2[i] : 0, table[idx[i]], seg_bits, k);
     }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* 16-bit baselines (Sec. IV-C): the nonzeros stored as IEEE binary16 (FP16) */
+/* or bfloat16 (BF16), converted once from FP64 by rounding to nearest, ties */
+/* to even, and widened back to FP64 exactly for the multiply-accumulate.    */
+
+/* Round |v| to a binary format with ebits exponent bits and mbits stored
+ * mantissa bits (FP16: 5, 10; BF16: 8, 7).  The quantum of v's binade (of the
+ * subnormal range below the smallest normal) divides |v| exactly; rint() in the
+ * default mode rounds the quotient to nearest even.  A carry into the next
+ * binade and overflow to infinity follow from the encoding. */
+static uint16_t round_small(double v, int ebits, int mbits)
+{
+    uint16_t sign = signbit(v) ? (uint16_t)(1u << (ebits + mbits)) : 0;
+    int bias = (1 << (ebits - 1)) - 1, emin = 1 - bias, emax = bias;
+    uint16_t inf = (uint16_t)(((1u << ebits) - 1) << mbits);
+    double a = fabs(v);
+    if (isnan(v)) return (uint16_t)(sign | inf | (1u << (mbits - 1)));
+    if (isinf(v)) return (uint16_t)(sign | inf);
+    if (a == 0.0) return sign;
+    int e;
+    frexp(a, &e);
+    int E = e - 1;                       /* a in [2^E, 2^(E+1)) */
+    int qexp = (E < emin ? emin : E) - mbits;
+    double n = rint(ldexp(a, -qexp));    /* integer, at most 2^(mbits+1) */
+    uint32_t ni = (uint32_t)n;
+    if (E < emin) return (uint16_t)(sign | ni);      /* n = 2^mbits lands on the smallest normal */
+    if (ni == (1u << (mbits + 1))) { ni >>= 1; E++; }
+    if (E > emax) return (uint16_t)(sign | inf);
+    return (uint16_t)(sign | ((uint32_t)(E + bias) << mbits) | (ni - (1u << mbits)));
+}
+
+static double widen_small(uint16_t h, int ebits, int mbits)
+{
+    int bias = (1 << (ebits - 1)) - 1;
+    int ef = (h >> mbits) & ((1 << ebits) - 1);
+    uint32_t man = h & ((1u << mbits) - 1);
+    double s = (h >> (ebits + mbits)) & 1 ? -1.0 : 1.0;
+    if (ef == (1 << ebits) - 1) return man ? NAN : s * INFINITY;
+    if (ef == 0) return s * ldexp((double)man, 1 - bias - mbits);
+    return s * ldexp((double)(man | (1u << mbits)), ef - bias - mbits);
+}
+
+/* kind 16: FP16, 17: BF16.  n_overflow counts finite values that became
+ * infinite (the FP16 arithmetic overflow the paper reports). */
+int orc_round16(int64_t n, const double* val, int kind, uint16_t* out, int64_t* n_overflow)
+{
+    if (kind != 16 && kind != 17) return ORC_ERR_INVALID;
+    int eb = kind == 16 ? 5 : 8, mb = kind == 16 ? 10 : 7;
+    int64_t ov = 0;
+    for (int64_t i = 0; i < n; i++) {
+        out[i] = round_small(val[i], eb, mb);
+        if (isfinite(val[i]) && ((out[i] >> mb) & ((1 << eb) - 1)) == (1 << eb) - 1) ov++;
+    }
+    if (n_overflow) *n_overflow = ov;
+    return ORC_OK;
+}
+
+int orc_widen16(int64_t n, const uint16_t* in, int kind, double* out)
+{
+    if (kind != 16 && kind != 17) return ORC_ERR_INVALID;
+    int eb = kind == 16 ? 5 : 8, mb = kind == 16 ? 10 : 7;
+    for (int64_t i = 0; i < n; i++) out[i] = widen_small(in[i], eb, mb);
     return ORC_OK;
 }
 
