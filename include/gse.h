@@ -44,6 +44,8 @@ extern "C" {
  * (values attached with gse_attach_values). */
 #define GSE_LEVEL_FP64     64
 #define GSE_LEVEL_FP32     32
+#define GSE_LEVEL_FP16     16   /* IEEE binary16 values (Sec. IV-C baseline) */
+#define GSE_LEVEL_BF16     17   /* bfloat16 values (Sec. IV-C baseline)      */
 
 /* Step-policy flags. */
 #define GSE_POLICY_NO_STAGNATION 1  /* never evaluate Conditions 1-3              */
@@ -101,6 +103,9 @@ typedef struct {
     int64_t bytes_level[3];       /* algorithmic bytes read+written by one SpMV   */
     int num_exp;                  /* table format: shared exponents in the table;
                                      0 for the per-group format                   */
+    int64_t overflow16;           /* finite values that became infinite when FP16
+                                     values were attached (the paper's FP16
+                                     arithmetic overflow); 0 otherwise            */
 } gse_matrix_info;
 
 /* Error name for a status code (static string). */
@@ -125,8 +130,12 @@ const char* gse_strerror(int status);
 int gse_encode(const gse_csr* csr, int group_size, const int* seg_bits, int n_seg,
                void* stream, gse_handle* out);
 
-/* Attach plain CSR values to a handle for the FP64 (bits = 64) or FP32
- * (bits = 32, rounded to nearest) baseline SpMV and solvers.  csr must have the
+/* Attach plain CSR values to a handle for a baseline SpMV and solvers:
+ * bits = GSE_LEVEL_FP64 (64), GSE_LEVEL_FP32 (32), GSE_LEVEL_FP16 (16, IEEE
+ * binary16) or GSE_LEVEL_BF16 (17, bfloat16); the narrower formats round each
+ * value to nearest even once from FP64 (Sec. IV-C stores the nonzeros in FP16 or
+ * BF16 and widens them to FP64 for the multiply-accumulate).  FP16 overflow is
+ * kept as infinity and counted in gse_matrix_info.overflow16.  csr must have the
  * structure the handle was encoded from. */
 int gse_attach_values(gse_handle h, const gse_csr* csr, int bits, void* stream);
 

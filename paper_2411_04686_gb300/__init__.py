@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libgse.so")
 
 OK, MAXITER, BREAKDOWN, NONFINITE, TIMEOUT = 0, 1, 2, 3, 4
 ERR_INVALID, ERR_NONFINITE, ERR_OOM, ERR_CUDA, ERR_UNSUPPORTED = -1, -2, -3, -4, -5
-LEVEL_FP64, LEVEL_FP32 = 64, 32
+LEVEL_FP64, LEVEL_FP32, LEVEL_FP16, LEVEL_BF16 = 64, 32, 16, 17
 POLICY_NO_STAGNATION, POLICY_FLOOR = 1, 2
 SCHEDULE_ROWS = 8
 
@@ -66,7 +66,7 @@ class MatrixInfo(ctypes.Structure):
     _fields_ = [("n_rows", _I64), ("n_cols", _I64), ("nnz", _I64), ("n_groups", _I64),
                 ("n_empty_rows", _I64), ("group_size", _I), ("n_seg", _I), ("seg_bits", _I * 3),
                 ("max_row_len", _I), ("mean_row_len", _D), ("schedule", _I),
-                ("bytes_level", _I64 * 3), ("num_exp", _I)]
+                ("bytes_level", _I64 * 3), ("num_exp", _I), ("overflow16", _I64)]
 
 
 _lib = None
@@ -169,8 +169,9 @@ SCALED_GMRES = Policy(l=150, t=30, m=30, rsd_limit=0.03, ndec_limit=8, reldec_li
 
 
 def fp64_policy(p: Policy, bits: int = 64) -> Policy:
-    """Same caps, plain CSR values (no stepping)."""
-    lv = LEVEL_FP64 if bits == 64 else LEVEL_FP32
+    """Same caps, plain CSR values (no stepping): bits = 64, 32, LEVEL_FP16 or
+    LEVEL_BF16 selects the attached baseline values."""
+    lv = {64: LEVEL_FP64, 32: LEVEL_FP32, LEVEL_FP16: LEVEL_FP16, LEVEL_BF16: LEVEL_BF16}[bits]
     return Policy(p.l, p.t, p.m, p.rsd_limit, p.ndec_limit, p.reldec_limit, p.max_iter, p.restart,
                   lv, lv, p.flags)
 

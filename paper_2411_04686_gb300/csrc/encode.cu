@@ -6,6 +6,9 @@
 #include <cstring>
 #include <vector>
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "spmv_core.cuh"
 
 namespace gse {
@@ -312,6 +315,26 @@ __global__ void k_scatter_rows(const int* flag, const int* pos, int64_t n, int32
         if (flag[r]) dst[pos[r]] = (int32_t)r;
 }
 
+// 16-bit baselines: round to nearest even once from FP64 (cuda_fp16 /
+// cuda_bf16 conversions); count finite values that became infinite.
+__global__ void k_round16(const double* val, int64_t nnz, int64_t nnz_pad, int kind, uint16_t* out,
+                          unsigned long long* n_overflow) {
+    unsigned long long ov = 0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz_pad; e += (int64_t)gridDim.x * blockDim.x) {
+        const double v = e < nnz ? val[e] : 0.0;
+        uint16_t b;
+        if (kind == GSE_LEVEL_FP16) {
+            b = __half_as_ushort(__double2half(v));
+            ov += isfinite(v) && (b & 0x7C00u) == 0x7C00u;
+        } else {
+            b = __bfloat16_as_ushort(__double2bfloat16(v));
+            ov += isfinite(v) && (b & 0x7F80u) == 0x7F80u;
+        }
+        out[e] = b;
+    }
+    if (ov) atomicAdd(n_overflow, ov);
+}
+
 __global__ void k_pad_values(const double* val, int64_t nnz, int64_t nnz_pad, double* v64, float* v32) {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz_pad; e += (int64_t)gridDim.x * blockDim.x) {
         const double v = e < nnz ? val[e] : 0.0;
@@ -342,7 +365,7 @@ static unsigned grid_for(int64_t n, int threads = 256) {
 static void free_all(gse_matrix* h) {
     void* bufs[] = {h->buf_col, h->buf_head, h->buf_tail1, h->buf_t2hi, h->buf_t2lo, h->buf_gexp,
                     h->buf_rowend, h->buf_blk_row0, h->buf_nzrow, h->buf_empty, h->buf_row_ptr,
-                    h->buf_val64, h->buf_val32, h->buf_carry, h->buf_part, h->buf_etab,
+                    h->buf_val64, h->buf_val32, h->buf_val16, h->buf_valbf, h->buf_carry, h->buf_part, h->buf_etab,
                     h->red_partial, h->red_counter, h->red_result, h->d_err};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -663,7 +686,8 @@ extern "C" int gse_export_table(gse_handle h, int16_t* table, int* n_table, uint
 }
 
 extern "C" int gse_attach_values(gse_handle h, const gse_csr* csr, int bits, void* stream) {
-    if (!h || !csr || (bits != 64 && bits != 32)) return GSE_ERR_INVALID;
+    if (!h || !csr || (bits != 64 && bits != 32 && bits != GSE_LEVEL_FP16 && bits != GSE_LEVEL_BF16))
+        return GSE_ERR_INVALID;
     if (csr->nnz != h->v.nnz || csr->n_rows != h->v.n_rows || (csr->nnz > 0 && !csr->val)) return GSE_ERR_INVALID;
     cudaStream_t s = (cudaStream_t)stream;
     const double* val = csr->val;
@@ -676,6 +700,31 @@ extern "C" int gse_attach_values(gse_handle h, const gse_csr* csr, int bits, voi
     double* v64 = nullptr;
     float* v32 = nullptr;
     int rc = GSE_OK;
+    if (bits == GSE_LEVEL_FP16 || bits == GSE_LEVEL_BF16) {
+        void*& buf = bits == GSE_LEVEL_FP16 ? h->buf_val16 : h->buf_valbf;
+        uint16_t* v16 = nullptr;
+        unsigned long long* d_ov = nullptr;
+        if (!buf) rc = dev_alloc(&v16, (size_t)h->v.nnz_pad, &h->bytes_matrix);
+        if (rc == GSE_OK && v16) buf = v16;
+        if (rc == GSE_OK && cudaMalloc(&d_ov, sizeof(unsigned long long)) != cudaSuccess) rc = GSE_ERR_OOM;
+        if (rc == GSE_OK) {
+            cudaMemsetAsync(d_ov, 0, sizeof(unsigned long long), s);
+            k_round16<<<grid_for(h->v.nnz_pad), 256, 0, s>>>(val, h->v.nnz, h->v.nnz_pad, bits, (uint16_t*)buf, d_ov);
+            unsigned long long ov = 0;
+            cudaMemcpyAsync(&ov, d_ov, sizeof(ov), cudaMemcpyDeviceToHost, s);
+            if (cudaStreamSynchronize(s) != cudaSuccess) rc = GSE_ERR_CUDA;
+            if (bits == GSE_LEVEL_FP16) h->overflow16 = (int64_t)ov;
+            if (bits == GSE_LEVEL_FP16) h->v.val16 = (const uint16_t*)buf;
+            else h->v.valbf = (const uint16_t*)buf;
+        }
+        if (d_ov) cudaFree(d_ov);
+        if (tmp) {
+            cudaStreamSynchronize(s);
+            cudaFree(tmp);
+        }
+        if (rc == GSE_OK && cudaGetLastError() != cudaSuccess) rc = GSE_ERR_CUDA;
+        return rc;
+    }
     if (bits == 64 && !h->buf_val64) rc = dev_alloc(&v64, (size_t)h->v.nnz_pad, &h->bytes_matrix);
     if (bits == 32 && !h->buf_val32) rc = dev_alloc(&v32, (size_t)h->v.nnz_pad, &h->bytes_matrix);
     if (rc == GSE_OK) {
@@ -748,6 +797,8 @@ extern "C" int gse_decode(gse_handle h, int k, double* vals, void* stream) {
         }
     } else if (k == GSE_LEVEL_FP64 && h->v.val64) k_decode<SRC_FP64, 0><<<g, 256, 0, s>>>(h->v, vals);
     else if (k == GSE_LEVEL_FP32 && h->v.val32) k_decode<SRC_FP32, 0><<<g, 256, 0, s>>>(h->v, vals);
+    else if (k == GSE_LEVEL_FP16 && h->v.val16) k_decode<SRC_FP16, 0><<<g, 256, 0, s>>>(h->v, vals);
+    else if (k == GSE_LEVEL_BF16 && h->v.valbf) k_decode<SRC_BF16, 0><<<g, 256, 0, s>>>(h->v, vals);
     else return GSE_ERR_INVALID;
     return cudaGetLastError() == cudaSuccess ? GSE_OK : GSE_ERR_CUDA;
 }
@@ -767,6 +818,7 @@ extern "C" int gse_matrix_get_info(gse_handle h, gse_matrix_info* info) {
     info->mean_row_len = h->mean_row_len;
     info->schedule = units_per_lane(h);
     info->num_exp = h->num_exp;
+    info->overflow16 = h->overflow16;
     // algorithmic bytes: col + live segments + group exponent per nonzero,
     // row_ptr, x read once, y written once
     const double nnz = (double)h->v.nnz, n = (double)h->v.n_rows, nc = (double)h->v.n_cols;

@@ -300,12 +300,7 @@ static void gm_release(GmWork& w) {
     if (w.hst) cudaFreeHost(w.hst);
 }
 
-static bool level_ok_gm(const gse_matrix* h, int k) {
-    if (k >= 1 && k <= h->n_seg) return true;
-    if (k == GSE_LEVEL_FP64) return h->v.val64 != nullptr;
-    if (k == GSE_LEVEL_FP32) return h->v.val32 != nullptr;
-    return false;
-}
+static bool level_ok_gm(const gse_matrix* h, int k) { return level_available(h, k); }
 
 extern "C" int gse_gmres(gse_handle h, const double* b, double* x, double tol, const gse_step_policy* pol,
                          gse_solve_info* info, void* stream) {

@@ -52,6 +52,8 @@ struct MatView {
     const int32_t* row_ptr;
     const double* val64;
     const float* val32;
+    const uint16_t* val16;     // FP16 baseline values (bit patterns)
+    const uint16_t* valbf;     // BF16 baseline values (bit patterns)
     double* carry;
     double* part;
     int64_t nnz, nnz_pad, n_rows, n_cols, n_nonempty, n_empty;
@@ -106,6 +108,9 @@ struct gse_matrix {
     void* buf_row_ptr;
     void* buf_val64;
     void* buf_val32;
+    void* buf_val16;
+    void* buf_valbf;
+    int64_t overflow16;  // FP16 values that overflowed at attach
     void* buf_carry;
     void* buf_part;
     // small scratch for grid reductions
@@ -133,6 +138,16 @@ namespace gse {
 
 inline int units_per_lane(const gse_matrix* h) {
     return h->schedule_forced ? h->schedule_forced : h->schedule_auto;
+}
+
+// A level the handle can run: a GSE level 1..n_seg or an attached baseline.
+inline bool level_available(const gse_matrix* h, int k) {
+    if (k >= 1 && k <= h->n_seg) return true;
+    if (k == GSE_LEVEL_FP64) return h->v.val64 != nullptr;
+    if (k == GSE_LEVEL_FP32) return h->v.val32 != nullptr;
+    if (k == GSE_LEVEL_FP16) return h->v.val16 != nullptr;
+    if (k == GSE_LEVEL_BF16) return h->v.valbf != nullptr;
+    return false;
 }
 
 // SpMV launch (spmv.cu).  Epilogue kinds:

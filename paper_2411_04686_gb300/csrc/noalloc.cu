@@ -86,12 +86,7 @@ __global__ void k_na_norm2(const double* __restrict__ v, int64_t n, double* out)
     if (threadIdx.x == 0) *out = a;
 }
 
-bool level_valid_na(const gse_matrix* h, int k) {
-    if (k >= 1 && k <= h->n_seg) return true;
-    if (k == GSE_LEVEL_FP64) return h->v.val64 != nullptr;
-    if (k == GSE_LEVEL_FP32) return h->v.val32 != nullptr;
-    return false;
-}
+bool level_valid_na(const gse_matrix* h, int k) { return level_available(h, k); }
 
 }  // namespace
 }  // namespace gse

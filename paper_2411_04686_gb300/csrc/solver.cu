@@ -90,6 +90,8 @@ __device__ __forceinline__ double eng_pipe(int k, const MatView& m, const double
         case 2: return spmv_chunks_block<2, 0, 1, ITER, !ITER, ENG_STAGES>(m, x, e, sc0, scs, nch, chunk_stage_layout<2, 0, 1>(ENG_WARPS, m.r_lo), smem, err);
         case 3: return spmv_chunks_block<3, -1, 1, ITER, !ITER, ENG_STAGES>(m, x, e, sc0, scs, nch, chunk_stage_layout<3, -1, 1>(ENG_WARPS, m.r_lo), smem, err);
         case SRC_FP32: return spmv_chunks_block<SRC_FP32, 0, 1, ITER, !ITER, ENG_STAGES>(m, x, e, sc0, scs, nch, chunk_stage_layout<SRC_FP32, 0, 1>(ENG_WARPS, m.r_lo), smem, err);
+        case SRC_FP16: return spmv_chunks_block<SRC_FP16, 0, 1, ITER, !ITER, ENG_STAGES>(m, x, e, sc0, scs, nch, chunk_stage_layout<SRC_FP16, 0, 1>(ENG_WARPS, m.r_lo), smem, err);
+        case SRC_BF16: return spmv_chunks_block<SRC_BF16, 0, 1, ITER, !ITER, ENG_STAGES>(m, x, e, sc0, scs, nch, chunk_stage_layout<SRC_BF16, 0, 1>(ENG_WARPS, m.r_lo), smem, err);
         default: return spmv_chunks_block<SRC_FP64, 0, 1, ITER, !ITER, ENG_STAGES>(m, x, e, sc0, scs, nch, chunk_stage_layout<SRC_FP64, 0, 1>(ENG_WARPS, m.r_lo), smem, err);
     }
 }
@@ -113,6 +115,8 @@ __device__ __forceinline__ double eng_rows(int k, const MatView& m, const double
                 return spmv_rows_block<3, 4, ITER, !ITER, ENG_ROW_STAGES>(m, x, e, sb0, sbs, nsb, row_stage_layout<3, -1>(span, m.r_lo), smem, err);
             return spmv_rows_block<3, -1, ITER, !ITER, ENG_ROW_STAGES>(m, x, e, sb0, sbs, nsb, row_stage_layout<3, -1>(span, m.r_lo), smem, err);
         case SRC_FP32: return spmv_rows_block<SRC_FP32, 0, ITER, !ITER, ENG_ROW_STAGES>(m, x, e, sb0, sbs, nsb, row_stage_layout<SRC_FP32, 0>(span, m.r_lo), smem, err);
+        case SRC_FP16: return spmv_rows_block<SRC_FP16, 0, ITER, !ITER, ENG_ROW_STAGES>(m, x, e, sb0, sbs, nsb, row_stage_layout<SRC_FP16, 0>(span, m.r_lo), smem, err);
+        case SRC_BF16: return spmv_rows_block<SRC_BF16, 0, ITER, !ITER, ENG_ROW_STAGES>(m, x, e, sb0, sbs, nsb, row_stage_layout<SRC_BF16, 0>(span, m.r_lo), smem, err);
         default: return spmv_rows_block<SRC_FP64, 0, ITER, !ITER, ENG_ROW_STAGES>(m, x, e, sb0, sbs, nsb, row_stage_layout<SRC_FP64, 0>(span, m.r_lo), smem, err);
     }
 }
@@ -669,12 +673,7 @@ extern "C" void gse_engine_destroy(gse_engine e) {
     delete e;
 }
 
-static bool level_valid(const gse_matrix* h, int k) {
-    if (k >= 1 && k <= h->n_seg) return true;
-    if (k == GSE_LEVEL_FP64) return h->v.val64 != nullptr;
-    if (k == GSE_LEVEL_FP32) return h->v.val32 != nullptr;
-    return false;
-}
+static bool level_valid(const gse_matrix* h, int k) { return level_available(h, k); }
 
 extern "C" int gse_engine_submit(gse_engine e, gse_handle h, const double* b, double* x, double tol,
                                  const gse_step_policy* pol, int* slot_out) {

@@ -65,6 +65,8 @@ static RowsKernel pick_rows_t(int k, int r_lo, RowStage* L, int span, bool tbl) 
             if (r_lo == 0) return k_spmv_rows<3, 0, RESID, STAGES>;
             return k_spmv_rows<3, -1, RESID, STAGES>;
         case SRC_FP32: *L = row_stage_layout<SRC_FP32, 0>(span, r_lo); return k_spmv_rows<SRC_FP32, 0, RESID, STAGES>;
+        case SRC_FP16: *L = row_stage_layout<SRC_FP16, 0>(span, r_lo); return k_spmv_rows<SRC_FP16, 0, RESID, STAGES>;
+        case SRC_BF16: *L = row_stage_layout<SRC_BF16, 0>(span, r_lo); return k_spmv_rows<SRC_BF16, 0, RESID, STAGES>;
         default: *L = row_stage_layout<SRC_FP64, 0>(span, r_lo); return k_spmv_rows<SRC_FP64, 0, RESID, STAGES>;
     }
 }
@@ -168,6 +170,8 @@ static KernelPick pick_kernel_tbl(int k, int r_lo) {
         case 2: return pick_one<2, 0, 1, RESID, true>(r_lo);
         case 3: return r_lo == 4 ? pick_one<3, 4, 1, RESID, true>(r_lo) : pick_one<3, -1, 1, RESID, true>(r_lo);
         case SRC_FP32: return pick_one<SRC_FP32, 0, 1, RESID>(r_lo);
+        case SRC_FP16: return pick_one<SRC_FP16, 0, 1, RESID>(r_lo);
+        case SRC_BF16: return pick_one<SRC_BF16, 0, 1, RESID>(r_lo);
         default: return pick_one<SRC_FP64, 0, 1, RESID>(r_lo);
     }
 }
@@ -185,6 +189,8 @@ static KernelPick pick_kernel_t(int k, int r_lo, int upl) {
                 default: return pick_upl<3, 16, RESID>(upl, r_lo);
             }
         case SRC_FP32: return pick_upl<SRC_FP32, 0, RESID>(upl, r_lo);
+        case SRC_FP16: return pick_one<SRC_FP16, 0, 1, RESID>(r_lo);     // 16-bit baselines: one unit per lane
+        case SRC_BF16: return pick_one<SRC_BF16, 0, 1, RESID>(r_lo);
         default: return pick_upl<SRC_FP64, 0, RESID>(upl, r_lo);
     }
 }
@@ -220,7 +226,7 @@ static int resident_blocks(const KernelPick& kp) {
 int launch_spmv(gse_matrix* h, int k, int epi, const SpmvArgs& a, cudaStream_t s, int upl_override) {
     int upl = upl_override ? upl_override : units_per_lane(h);
     if (upl == GSE_SCHEDULE_ROWS) return launch_rows(h, k, epi, a, s);
-    if (h->v.tbl) upl = 1;                     // the table format runs one unit per lane
+    if (h->v.tbl || src16(k)) upl = 1;         // the table format and the 16-bit baselines run one unit per lane
     const KernelPick kp = pick_kernel(k, h->v.r_lo, upl, epi == EPI_RESID, h->v.tbl != 0);
     const int64_t ch = 256 * upl;
     const int64_t n_chunks = (h->v.nnz + ch - 1) / ch;
@@ -250,12 +256,7 @@ int launch_spmv(gse_matrix* h, int k, int epi, const SpmvArgs& a, cudaStream_t s
 
 using namespace gse;
 
-static bool level_ok(gse_matrix* h, int k) {
-    if (k >= 1 && k <= h->n_seg) return true;
-    if (k == GSE_LEVEL_FP64) return h->v.val64 != nullptr;
-    if (k == GSE_LEVEL_FP32) return h->v.val32 != nullptr;
-    return false;
-}
+static bool level_ok(gse_matrix* h, int k) { return level_available(h, k); }
 
 extern "C" int gse_spmv(gse_handle h, int k, const double* x, double* y, void* stream) {
     if (!h || !x || !y || !level_ok(h, k)) return GSE_ERR_INVALID;

@@ -19,8 +19,11 @@
 
 namespace gse {
 
-// Value sources: K = 1, 2, 3 are GSE levels; K = 32 / 64 the plain CSR baselines.
-enum { SRC_FP32 = 32, SRC_FP64 = 64 };
+// Value sources: K = 1, 2, 3 are GSE levels; K = 16 / 17 / 32 / 64 the plain CSR
+// baselines in FP16 / BF16 / FP32 / FP64 (the level selectors of include/gse.h).
+enum { SRC_FP16 = 16, SRC_BF16 = 17, SRC_FP32 = 32, SRC_FP64 = 64 };
+// 16-bit value sources (the baselines stored in 2 bytes per nonzero).
+__host__ __device__ constexpr bool src16(int K) { return K == SRC_FP16 || K == SRC_BF16; }
 
 // ---- decode (Alg. 2 and the concatenated tails) --------------------------------
 
@@ -112,12 +115,35 @@ __device__ __forceinline__ double widen_f32(uint32_t f) {
     if (e == 0xFFu) return __hiloint2double((int)(sign | 0x7FF00000u | (man >> 3)), (int)(man << 29));
     if (e == 0) {
         if (man == 0) return __hiloint2double((int)sign, 0);
-        const int lz = __clz(man) - 8;               // normalise the subnormal
-        man = (man << (lz + 1)) & 0x7FFFFFu;
-        const uint32_t ed = 1023 - 127 - lz;
+        const int lz = __clz(man) - 8;               // leading one at bit 23 - lz
+        man = (man << lz) & 0x7FFFFFu;               // ... moved to bit 23 and dropped
+        const uint32_t ed = 1023 - 126 - lz;         // man * 2^-149 = 1.f * 2^(-126 - lz)
         return __hiloint2double((int)(sign | (ed << 20) | (man >> 3)), (int)(man << 29));
     }
     return __hiloint2double((int)(sign | ((e + 896u) << 20) | (man >> 3)), (int)(man << 29));
+}
+
+// binary16 -> FP64 with integer operations (exact; subnormals normalised by CLZ).
+__device__ __forceinline__ double widen_f16(uint32_t h) {
+    const uint32_t sign = (h & 0x8000u) << 16;
+    const uint32_t e = (h >> 10) & 0x1Fu;
+    uint32_t man = h & 0x3FFu;
+    if (e == 0x1Fu) return __hiloint2double((int)(sign | 0x7FF00000u | (man << 10)), 0);
+    if (e == 0) {
+        if (man == 0) return __hiloint2double((int)sign, 0);
+        const int lz = __clz(man) - 21;              // leading one at bit 10 - lz
+        man = (man << lz) & 0x3FFu;                  // ... moved to bit 10 and dropped
+        // man * 2^-24 = 1.f * 2^(-14 - lz)
+        return __hiloint2double((int)(sign | ((uint32_t)(1023 - 14 - lz) << 20) | (man << 10)), 0);
+    }
+    return __hiloint2double((int)(sign | ((e + 1008u) << 20) | (man << 10)), 0);
+}
+// bfloat16 -> FP64: bfloat16 is the top half of a binary32.
+__device__ __forceinline__ double widen_bf16(uint32_t b) { return widen_f32(b << 16); }
+template <int K>
+__device__ __forceinline__ double widen16(uint32_t v) {
+    if constexpr (K == SRC_FP16) return widen_f16(v);
+    else return widen_bf16(v);
 }
 
 __device__ __forceinline__ uint32_t u16_of(const uint4& w, int i) {
@@ -146,6 +172,10 @@ __device__ __forceinline__ void load_unit(const MatView& m, int64_t u, int* col,
         const uint4 fa = __ldcs(f4), fb = __ldcs(f4 + 1);
         a[0] = widen_f32(fa.x); a[1] = widen_f32(fa.y); a[2] = widen_f32(fa.z); a[3] = widen_f32(fa.w);
         a[4] = widen_f32(fb.x); a[5] = widen_f32(fb.y); a[6] = widen_f32(fb.z); a[7] = widen_f32(fb.w);
+    } else if constexpr (src16(K)) {
+        const uint4 w = __ldcs(reinterpret_cast<const uint4*>(K == SRC_FP16 ? m.val16 : m.valbf) + u);
+#pragma unroll
+        for (int i = 0; i < 8; i++) a[i] = widen16<K>(u16_of(w, i));
     } else {
         const int Eg0 = m.tbl ? 0 : (int)__ldg(m.gexp + ((u * GSE_UNIT) >> m.g_shift));
         const uint4 hw = __ldcs(reinterpret_cast<const uint4*>(m.head) + u);

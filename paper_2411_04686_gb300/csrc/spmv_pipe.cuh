@@ -99,6 +99,7 @@ __host__ __device__ inline RowStage row_stage_layout(int span, int r_lo) {
     int v;
     if (K == SRC_FP64) v = span * 8;
     else if (K == SRC_FP32) v = span * 4;
+    else if (src16(K)) v = span * 2;
     else v = span * 2 * (K >= 3 ? 3 : K) + (K >= 3 ? span * (R < 0 ? r_lo : R) / 8 : 0);
     L.off_gx = L.off_v + ((v + 127) / 128) * 128;
     const int gx = (span / 8 + 16) * 2;    // group exponents of the span (groups >= 8), 8-group aligned ends
@@ -133,8 +134,9 @@ __device__ __forceinline__ void issue_rows(const MatView& m, const RowStage& L, 
     uint32_t vbytes;
     if constexpr (K == SRC_FP64) vbytes = n * 8;
     else if constexpr (K == SRC_FP32) vbytes = n * 4;
+    else if constexpr (src16(K)) vbytes = n * 2;
     else vbytes = n * 2 * (K >= 3 ? 3 : K) + (K >= 3 ? n * r / 8 : 0);
-    const bool gse_src = K != SRC_FP64 && K != SRC_FP32 && !TBL;   // the table format has no group exponents
+    const bool gse_src = K <= 3 && !TBL;     // the baselines and the table format have no group exponents
     mbar_expect_tx(bar, n * 4 + vbytes + (gse_src ? gx_bytes : 0));
     const uint32_t s = smem_u32(stage);
     bulk_g2s(s, m.col + rb.e_lo, n * 4, bar);
@@ -142,6 +144,8 @@ __device__ __forceinline__ void issue_rows(const MatView& m, const RowStage& L, 
         bulk_g2s(s + L.off_v, m.val64 + rb.e_lo, n * 8, bar);
     } else if constexpr (K == SRC_FP32) {
         bulk_g2s(s + L.off_v, m.val32 + rb.e_lo, n * 4, bar);
+    } else if constexpr (src16(K)) {
+        bulk_g2s(s + L.off_v, (K == SRC_FP16 ? m.val16 : m.valbf) + rb.e_lo, n * 2, bar);
     } else {
         const uint32_t sp2 = (uint32_t)L.span * 2;
         bulk_g2s(s + L.off_v, m.head + rb.e_lo, n * 2, bar);
@@ -164,6 +168,8 @@ __device__ __forceinline__ double row_value(const MatView& m, const RowStage& L,
         return reinterpret_cast<const double*>(stage + L.off_v)[i];
     } else if constexpr (K == SRC_FP32) {
         return widen_f32(reinterpret_cast<const uint32_t*>(stage + L.off_v)[i]);
+    } else if constexpr (src16(K)) {
+        return widen16<K>(reinterpret_cast<const uint16_t*>(stage + L.off_v)[i]);
     } else {
         const int Eg = TBL ? (int)etab[etab_index(m, cw)]
                            : (int)reinterpret_cast<const uint16_t*>(stage + L.off_gx)[(i >> m.g_shift) + goff];
@@ -338,6 +344,7 @@ __host__ __device__ inline ChunkStage chunk_stage_layout(int W, int r_lo) {
     int v;
     if (K == SRC_FP64) v = e * 8;
     else if (K == SRC_FP32) v = e * 4;
+    else if (src16(K)) v = e * 2;
     else v = e * 2 * (K >= 3 ? 3 : K) + (K >= 3 ? e * (R < 0 ? r_lo : R) / 8 : 0);
     L.off_re = L.off_v + ((v + 127) / 128) * 128;
     L.off_gx = L.off_re + ((e / 8 + 127) / 128) * 128;
@@ -357,8 +364,9 @@ __device__ __forceinline__ void issue_superchunk(const MatView& m, const ChunkSt
     uint32_t vbytes;
     if constexpr (K == SRC_FP64) vbytes = e * 8;
     else if constexpr (K == SRC_FP32) vbytes = e * 4;
+    else if constexpr (src16(K)) vbytes = e * 2;
     else vbytes = e * 2 * (K >= 3 ? 3 : K) + (K >= 3 ? e * r / 8 : 0);
-    const bool gse_src = K != SRC_FP64 && K != SRC_FP32 && !TBL;
+    const bool gse_src = K <= 3 && !TBL;
     mbar_expect_tx(bar, e * 4 + vbytes + e / 8 + (gse_src ? gx_bytes : 0));
     const uint32_t s = smem_u32(stage);
     const uint32_t E = (uint32_t)(L.nch * L.ch);    // full-stage stride of the segment arrays
@@ -367,6 +375,8 @@ __device__ __forceinline__ void issue_superchunk(const MatView& m, const ChunkSt
         bulk_g2s(s + L.off_v, m.val64 + e0, e * 8, bar);
     } else if constexpr (K == SRC_FP32) {
         bulk_g2s(s + L.off_v, m.val32 + e0, e * 4, bar);
+    } else if constexpr (src16(K)) {
+        bulk_g2s(s + L.off_v, (K == SRC_FP16 ? m.val16 : m.valbf) + e0, e * 2, bar);
     } else {
         bulk_g2s(s + L.off_v, m.head + e0, e * 2, bar);
         if constexpr (K >= 2) bulk_g2s(s + L.off_v + E * 2, m.tail1 + e0, e * 2, bar);
@@ -399,6 +409,10 @@ __device__ __forceinline__ void unit_values_blk(const MatView& m, const ChunkSta
         const uint4 fa = f4[0], fb = f4[1];
         a[0] = widen_f32(fa.x); a[1] = widen_f32(fa.y); a[2] = widen_f32(fa.z); a[3] = widen_f32(fa.w);
         a[4] = widen_f32(fb.x); a[5] = widen_f32(fb.y); a[6] = widen_f32(fb.z); a[7] = widen_f32(fb.w);
+    } else if constexpr (src16(K)) {
+        const uint4 w = reinterpret_cast<const uint4*>(stage + L.off_v)[u];
+#pragma unroll
+        for (int i = 0; i < 8; i++) a[i] = widen16<K>(u16_of(w, i));
     } else {
         const uint16_t* gx = reinterpret_cast<const uint16_t*>(stage + L.off_gx);
         const int Eg0 = TBL ? 0 : (int)gx[(u * GSE_UNIT) >> m.g_shift];
