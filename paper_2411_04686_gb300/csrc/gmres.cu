@@ -100,14 +100,43 @@ __global__ void k_gm_norm(GmState* st, const double* __restrict__ v, int64_t n, 
 // pass 1 (re-orthogonalisation, only if flagged): c_j = scale_j (w . V_j).
 // The i + 2 sums are taken 8 at a time in registers; block partials go to
 // shared memory, then one grid-level reduction for all of them.
+// Warp sums of 8 values per lane with 9 FP64 additions per lane (instead of 8
+// separate 5-step reductions, 40 additions): at each of the first three
+// exchanges a lane keeps half of its values and adds the partner's copy of
+// them, then the last value is summed over the 4-lane group.  Afterwards lane
+// L holds the full sum of value 4*bit4(L) + 2*bit3(L) + bit2(L).
+__device__ __forceinline__ double warp_sum8(const double* a, int lane) {
+    const unsigned FULL = 0xFFFFFFFFu;
+    double b[4], c[2];
+    const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+        const double send = h16 ? a[u] : a[u + 4];
+        b[u] = (h16 ? a[u + 4] : a[u]) + __shfl_xor_sync(FULL, send, 16);
+    }
+#pragma unroll
+    for (int u = 0; u < 2; u++) {
+        const double send = h8 ? b[u] : b[u + 2];
+        c[u] = (h8 ? b[u + 2] : b[u]) + __shfl_xor_sync(FULL, send, 8);
+    }
+    double d = (h4 ? c[1] : c[0]) + __shfl_xor_sync(FULL, h4 ? c[0] : c[1], 4);
+    d += __shfl_xor_sync(FULL, d, 2);
+    d += __shfl_xor_sync(FULL, d, 1);
+    return d;
+}
+
+// h_j = v_j . w for j <= i and |w|^2 (CGS step; pass 1 is the DGKS correction),
+// 8 dot products per sweep over w.
 __global__ void __launch_bounds__(256) k_gm_dots(GmState* st, const double* __restrict__ V, int64_t n, int i,
                                                   int pass, double* partial, unsigned* counter) {
     __shared__ double red[32];
     __shared__ double bpart[GM_MAX_RESTART + 2];
+    __shared__ double wsum[8][8];
     __shared__ bool last;
     if (st->stop || (pass == 1 && !st->need_reorth)) return;
     const double* w = V + (size_t)(i + 1) * n;
     const int nv = i + 2;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int jb = 0; jb < nv; jb += 8) {
         double a[8];
 #pragma unroll
@@ -120,11 +149,15 @@ __global__ void __launch_bounds__(256) k_gm_dots(GmState* st, const double* __re
                 if (j < nv) a[u] = fma(wt, j <= i ? V[(size_t)j * n + t] : wt, a[u]);
             }
         }
-#pragma unroll
-        for (int u = 0; u < 8; u++) {
-            const double bs = block_sum(a[u], red);
-            if (threadIdx.x == 0 && jb + u < nv) bpart[jb + u] = bs;
+        const double d = warp_sum8(a, lane);
+        if ((lane & 3) == 0) wsum[warp][((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1)] = d;
+        __syncthreads();
+        if (threadIdx.x < 8) {
+            double sum = 0.0;
+            for (int wi = 0; wi < (int)(blockDim.x >> 5); wi++) sum += wsum[wi][threadIdx.x];
+            if (jb + (int)threadIdx.x < nv) bpart[jb + threadIdx.x] = sum;
         }
+        __syncthreads();
     }
     if (threadIdx.x == 0) {
         for (int j = 0; j < nv; j++) partial[(size_t)j * gridDim.x + blockIdx.x] = bpart[j];
@@ -151,9 +184,6 @@ __global__ void __launch_bounds__(256) k_gm_dots(GmState* st, const double* __re
         }
     }
 }
-
-// w = scale_i w_raw - sum_j h_j scale_j V_j (pass 0), or w -= sum_j c_j scale_j
-// V_j (pass 1); then ||w||, and the re-orthogonalisation test.
 __global__ void __launch_bounds__(256) k_gm_axpy(GmState* st, double* __restrict__ V, int64_t n, int i, int pass,
                                                   double* partial, unsigned* counter) {
     __shared__ double red[32];
@@ -166,11 +196,26 @@ __global__ void __launch_bounds__(256) k_gm_axpy(GmState* st, double* __restrict
     __syncthreads();
     double* w = V + (size_t)(i + 1) * n;
     double acc = 0.0;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
-        double v = si * w[t];
-        for (int j = 0; j <= i; j++) v = fma(-coef[j], V[(size_t)j * n + t], v);
-        w[t] = v;
-        acc = fma(v, v, acc);
+    // four elements per thread, so each basis vector contributes four
+    // independent loads and FMAs (the chain over j is sequential per element)
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t0 < n; t0 += 4 * stride) {
+        double v[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) v[q] = t0 + q * stride < n ? si * w[t0 + q * stride] : 0.0;
+        for (int j = 0; j <= i; j++) {
+            const double c = -coef[j];
+            const double* vj = V + (size_t)j * n;
+#pragma unroll
+            for (int q = 0; q < 4; q++)
+                if (t0 + q * stride < n) v[q] = fma(c, vj[t0 + q * stride], v[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+            if (t0 + q * stride < n) {
+                w[t0 + q * stride] = v[q];
+                acc = fma(v[q], v[q], acc);
+            }
     }
     if (!gm_grid_sums(&acc, 1, partial, counter, red, tot)) return;
     if (threadIdx.x == 0) {
