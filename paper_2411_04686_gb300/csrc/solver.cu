@@ -74,25 +74,22 @@ __device__ __forceinline__ bool sys_grid_last(unsigned* counter, int nblk) {
 
 // ITER: q = A p with the p.q epilogue; RESID: y = b - A x, no dot.  The engine
 // runs one unit of 8 nonzeros per lane (chunks of 256), ENG_WARPS chunks per stage.
+// ITER: q = A p with the p.q epilogue; RESID: y = b - A x, no dot.  The
+// nonzero split runs the direct-load chunk loop (no stage ring): warp w of the
+// system's CTAs takes chunks w, w + W, ...
 template <bool ITER>
-__device__ __forceinline__ double eng_pipe(int k, const MatView& m, const double* x, const Epi& e, int64_t sc0,
-                                           int64_t scs, int64_t nch, unsigned char* smem, int* err) {
-    if (m.tbl) {                      // table format: the shared exponent comes with each col word
-        switch (k) {
-            case 1: return spmv_chunks_block<1, 0, 1, ITER, !ITER, ENG_STAGES, true>(m, x, e, sc0, scs, nch, chunk_stage_layout<1, 0, 1>(ENG_WARPS, m.r_lo), smem, err);
-            case 2: return spmv_chunks_block<2, 0, 1, ITER, !ITER, ENG_STAGES, true>(m, x, e, sc0, scs, nch, chunk_stage_layout<2, 0, 1>(ENG_WARPS, m.r_lo), smem, err);
-            case 3: return spmv_chunks_block<3, -1, 1, ITER, !ITER, ENG_STAGES, true>(m, x, e, sc0, scs, nch, chunk_stage_layout<3, -1, 1>(ENG_WARPS, m.r_lo), smem, err);
-            default: break;
-        }
-    }
+__device__ __forceinline__ double eng_pipe(int k, const MatView& m, const double* x, const Epi& e, int64_t w0,
+                                           int64_t ws, int64_t nch) {
     switch (k) {
-        case 1: return spmv_chunks_block<1, 0, 1, ITER, !ITER, ENG_STAGES>(m, x, e, sc0, scs, nch, chunk_stage_layout<1, 0, 1>(ENG_WARPS, m.r_lo), smem, err);
-        case 2: return spmv_chunks_block<2, 0, 1, ITER, !ITER, ENG_STAGES>(m, x, e, sc0, scs, nch, chunk_stage_layout<2, 0, 1>(ENG_WARPS, m.r_lo), smem, err);
-        case 3: return spmv_chunks_block<3, -1, 1, ITER, !ITER, ENG_STAGES>(m, x, e, sc0, scs, nch, chunk_stage_layout<3, -1, 1>(ENG_WARPS, m.r_lo), smem, err);
-        case SRC_FP32: return spmv_chunks_block<SRC_FP32, 0, 1, ITER, !ITER, ENG_STAGES>(m, x, e, sc0, scs, nch, chunk_stage_layout<SRC_FP32, 0, 1>(ENG_WARPS, m.r_lo), smem, err);
-        case SRC_FP16: return spmv_chunks_block<SRC_FP16, 0, 1, ITER, !ITER, ENG_STAGES>(m, x, e, sc0, scs, nch, chunk_stage_layout<SRC_FP16, 0, 1>(ENG_WARPS, m.r_lo), smem, err);
-        case SRC_BF16: return spmv_chunks_block<SRC_BF16, 0, 1, ITER, !ITER, ENG_STAGES>(m, x, e, sc0, scs, nch, chunk_stage_layout<SRC_BF16, 0, 1>(ENG_WARPS, m.r_lo), smem, err);
-        default: return spmv_chunks_block<SRC_FP64, 0, 1, ITER, !ITER, ENG_STAGES>(m, x, e, sc0, scs, nch, chunk_stage_layout<SRC_FP64, 0, 1>(ENG_WARPS, m.r_lo), smem, err);
+        case 1: return spmv_chunks_direct<1, 0, ITER, !ITER>(m, x, e, w0, ws, nch);
+        case 2: return spmv_chunks_direct<2, 0, ITER, !ITER>(m, x, e, w0, ws, nch);
+        case 3:
+            if (m.r_lo == 4) return spmv_chunks_direct<3, 4, ITER, !ITER>(m, x, e, w0, ws, nch);
+            return spmv_chunks_direct<3, -1, ITER, !ITER>(m, x, e, w0, ws, nch);
+        case SRC_FP32: return spmv_chunks_direct<SRC_FP32, 0, ITER, !ITER>(m, x, e, w0, ws, nch);
+        case SRC_FP16: return spmv_chunks_direct<SRC_FP16, 0, ITER, !ITER>(m, x, e, w0, ws, nch);
+        case SRC_BF16: return spmv_chunks_direct<SRC_BF16, 0, ITER, !ITER>(m, x, e, w0, ws, nch);
+        default: return spmv_chunks_direct<SRC_FP64, 0, ITER, !ITER>(m, x, e, w0, ws, nch);
     }
 }
 
@@ -148,8 +145,9 @@ __device__ __forceinline__ void p1_body(const SysDesc* __restrict__ sys, const i
     const int64_t nsb = (S.n + 32 * ENG_ROW_WARPS - 1) / (32 * ENG_ROW_WARPS);
     if (!ROWS) fill_empty_rows(m, e, (int64_t)lb * blockDim.x + threadIdx.x, (int64_t)nblk * blockDim.x);
     if (mode == MODE_ITER) {
+        const int64_t w0 = (int64_t)lb * ENG_WARPS + (threadIdx.x >> 5), ws = (int64_t)nblk * ENG_WARPS;
         const double dot = ROWS ? eng_rows<true>(k, m, x, e, lb, nblk, nsb, S.row_span, smem, S.err)
-                                : eng_pipe<true>(k, m, x, e, lb, nblk, S.n_chunks, smem, S.err);
+                                : eng_pipe<true>(k, m, x, e, w0, ws, S.n_chunks);
         double total;
         if (sys_grid_sum(dot, S.partial, S.counter, lb, nblk, red, &total) && threadIdx.x == 0) {
             // alpha = rho / p.Ap once per system here, not in every thread of P2
@@ -160,7 +158,8 @@ __device__ __forceinline__ void p1_body(const SysDesc* __restrict__ sys, const i
         }
     } else {
         if (ROWS) eng_rows<false>(k, m, x, e, lb, nblk, nsb, S.row_span, smem, S.err);
-        else eng_pipe<false>(k, m, x, e, lb, nblk, S.n_chunks, smem, S.err);
+        else eng_pipe<false>(k, m, x, e, (int64_t)lb * ENG_WARPS + (threadIdx.x >> 5), (int64_t)nblk * ENG_WARPS,
+                             S.n_chunks);
     }
 }
 

@@ -10,7 +10,6 @@ enum { MODE_ITER = 0, MODE_RESID_R = 1, MODE_RESID_T = 2, MODE_DONE = 3 };
 enum { PA_NONE = 0, PA_UPDATE = 1, PA_XONLY = 2, PA_COPY_R = 3, PA_COPY_Q = 4, PA_ZERO_X = 5 };
 constexpr int RING_MAX = 4096;
 constexpr int ENG_WARPS = 4;
-constexpr int ENG_STAGES = 3;       // stage ring of the nonzero split
 constexpr int ENG_ROW_STAGES = 2;   // stage ring of the row schedule (wide stages: fewer, more CTAs)
 constexpr int ENG_ROW_WARPS = 8;    // row schedule: CTAs of 8 warps, 256-row super-blocks
 
@@ -71,13 +70,8 @@ __global__ void k_cg_fix(const SysDesc* __restrict__ sys, const int2* __restrict
 __global__ void k_cg_p2(const SysDesc* __restrict__ sys, const int2* __restrict__ map);
 __global__ void k_cg_p3(const SysDesc* __restrict__ sys, const int2* __restrict__ map);
 
-// Shared memory of a P1 CTA on the nonzero split: the stage ring for the
-// largest value source (a system's level changes during the solve).
-inline size_t p1_smem() {
-    const int a = chunks_block_smem<ENG_STAGES, 1>(chunk_stage_layout<SRC_FP64, 0, 1>(ENG_WARPS, 16));
-    const int b = chunks_block_smem<ENG_STAGES, 1>(chunk_stage_layout<3, -1, 1>(ENG_WARPS, 16));
-    return (size_t)(a > b ? a : b);
-}
+// Shared memory of a P1 CTA on the nonzero split: none (direct loads).
+inline size_t p1_smem() { return 0; }
 
 // Shared memory of a P1 CTA on the row schedule for a stage span (nonzeros per
 // 256-row super-block), again for the largest value source.
@@ -120,7 +114,7 @@ inline void sys_partition(SysDesc& d, const gse_matrix* h, int num_sms) {
         const int64_t wave = (int64_t)num_sms * p1_occupancy(true, p1_rows_smem(d.row_span, d.m.r_lo));
         if (nbs > wave) nbs = wave;
     } else {
-        nbs = (d.n_chunks + ENG_WARPS - 1) / ENG_WARPS;                // super-chunks
+        nbs = (d.n_chunks + ENG_WARPS - 1) / ENG_WARPS;                // a chunk per warp
         const int64_t wave = (int64_t)num_sms * p1_occupancy(false, p1_smem());
         if (nbs > wave) nbs = wave;
     }

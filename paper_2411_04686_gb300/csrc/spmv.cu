@@ -25,6 +25,18 @@ __global__ void __launch_bounds__(spmv_warps<UPL>() * 32) k_spmv(MatView m, cons
     spmv_chunks_block<K, R, UPL, false, RESID, STAGES, TBL>(m, x, e, blockIdx.x, gridDim.x, n_chunks, L, smem, err);
 }
 
+// One unit of 8 per lane: the direct-load nonzero split (no stage ring), 8-warp CTAs.
+template <int K, int R, bool RESID>
+__global__ void __launch_bounds__(256) k_spmv_direct(MatView m, const double* __restrict__ x, Epi e, int64_t n_chunks,
+                                                     ChunkStage L, int* err, const int* gate) {
+    if (gate && *gate) return;
+    (void)L;
+    (void)err;
+    fill_empty_rows(m, e, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    spmv_chunks_direct<K, R, false, RESID>(m, x, e, gw, ((int64_t)gridDim.x * blockDim.x) >> 5, n_chunks);
+}
+
 // Finishes the rows that cross chunk boundaries (after k_spmv, same stream).
 template <int UPL>
 __global__ void __launch_bounds__(256) k_spmv_fix(MatView m, Epi e, int64_t n_chunks, const int* gate) {
@@ -85,7 +97,6 @@ static int rows_resident(RowsKernel fn, size_t smem) {
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return 0;
-    cudaFuncSetAttribute((const void*)fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, ROWS_WARPS * 32, smem) != cudaSuccess) return 0;
     if (nkeys < 256) {
@@ -107,7 +118,7 @@ static int launch_rows(gse_matrix* h, int k, int epi, const SpmvArgs& a, cudaStr
                           : pick_rows_t<false, 2>(k, h->v.r_lo, &L2, h->row_span256, tbl);
     const size_t smem3 = (size_t)rows_block_smem<3>(L3), smem2 = (size_t)rows_block_smem<2>(L2);
     const int nb3 = rows_resident(f3, smem3), nb2 = rows_resident(f2, smem2);
-    const bool two = nb2 > nb3;
+    const bool two = nb2 >= nb3;      // equal occupancy: the smaller ring leaves more L1 for the x gathers
     RowsKernel fn = two ? f2 : f3;
     const size_t smem = two ? smem2 : smem3;
     const RowStage L = two ? L2 : L3;
@@ -147,10 +158,24 @@ KernelPick pick_stages(int r_lo) {
 
 static int resident_blocks(const KernelPick& kp);
 
+template <int K, int R, bool RESID>
+KernelPick pick_direct(int r_lo) {
+    KernelPick kp;
+    kp.fn = k_spmv_direct<K, R, RESID>;
+    kp.warps = 8;
+    kp.L = chunk_stage_layout<K, R, 1>(8, r_lo);    // unused by the kernel
+    kp.smem = 0;
+    return kp;
+}
+
 template <int K, int R, int UPL, bool RESID, bool TBL = false>
 KernelPick pick_one(int r_lo) {
-    const KernelPick a = pick_stages<K, R, UPL, RESID, 3, TBL>(r_lo), b = pick_stages<K, R, UPL, RESID, 2, TBL>(r_lo);
-    return resident_blocks(b) > resident_blocks(a) ? b : a;
+    if constexpr (UPL == 1) {
+        return pick_direct<K, R, RESID>(r_lo);   // the exponent source (group or table) is read per unit or value
+    } else {
+        const KernelPick a = pick_stages<K, R, UPL, RESID, 3, TBL>(r_lo), b = pick_stages<K, R, UPL, RESID, 2, TBL>(r_lo);
+        return resident_blocks(b) >= resident_blocks(a) ? b : a;   // equal occupancy: 2 stages, more L1 for the gathers
+    }
 }
 
 template <int K, int R, bool RESID>
@@ -211,7 +236,6 @@ static int resident_blocks(const KernelPick& kp) {
         if (keys[i] == (const void*)kp.fn) return vals[i];
     if (kp.smem > 48 * 1024)
         cudaFuncSetAttribute((const void*)kp.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kp.smem);
-    cudaFuncSetAttribute((const void*)kp.fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kp.fn, kp.warps * 32, kp.smem) != cudaSuccess || nb < 1)
         nb = 1;

@@ -198,7 +198,7 @@ __device__ __forceinline__ void load_unit(const MatView& m, int64_t u, int* col,
             const uint32_t h = u16_of(hw, i);
             const int Eg = m.tbl ? (int)__ldg(m.etab + etab_index(m, col[i])) : Eg0;   // table format: per value
             if constexpr (K == 1) {
-                a[i] = decode_l1(h, Eg, m);
+                a[i] = decode_l1_f(h, Eg, (uint32_t)(Eg - m.W1 - 127) << 20, m);
             } else if constexpr (K == 2) {
                 a[i] = decode_l2(h, u16_of(t1w, i), Eg, m);
             } else {

@@ -1,8 +1,11 @@
-// spmv_pipe.cuh -- the GSE-SpMV main loop with TMA-staged chunks.
+// spmv_pipe.cuh -- the GSE-SpMV main loops.
 //
-// Both schedules stage the matrix through a ring of shared-memory stages per
-// CTA.  One producer thread fills a stage with a few large 1-D bulk copies
-// (cp.async.bulk, completion counted in bytes on a "full" mbarrier): column
+// The row schedule and the 2- and 4-unit nonzero split stage the matrix
+// through a ring of shared-memory stages per CTA; the default 1-unit nonzero
+// split (for scattered columns) loads straight from global memory instead, so
+// that the SM's L1 stays free for the random x gathers (spmv_chunks_direct).
+// In the staged loops one producer thread fills a stage with a few large 1-D
+// bulk copies (cp.async.bulk, completion counted in bytes on a "full" mbarrier): column
 // indices, the live segment arrays (or the CSR values of a baseline), row-end
 // bits and group exponents -- contiguous, 16-byte aligned slices of the HBM
 // arrays.  Every warp consumes its part, then arrives on the stage's "empty"
@@ -628,6 +631,109 @@ __device__ __forceinline__ double spmv_chunks_block(const MatView& m, const doub
         ephase ^= 1u << s;
     }
     if (!ok && lane == 0) atomicOr(err, 1);
+    return dot;
+}
+
+// ---- nonzero split, direct loads (one unit of 8 per lane) ----------------
+// The same chunk logic with no shared-memory staging: lane l of the warp that
+// owns chunk c loads unit 32c + l (two int4 of columns, one 128-bit word per
+// live segment, the group exponent, its byte of row-end bits) straight from
+// global memory -- coalesced across the warp -- and gathers x.  Without a
+// stage ring every SM keeps its whole L1 for the random x gathers, which is
+// what matrices with scattered columns are bound by; this is the default
+// nonzero-split kernel (the staged ring above serves 2 and 4 units per lane).
+template <int K, int R, bool DOT, bool RESID>
+__device__ __forceinline__ double compute_chunk_direct(const MatView& m, const Epi& e, int64_t c,
+                                                       const double* __restrict__ x) {
+    const unsigned FULL = 0xFFFFFFFFu;
+    const int lane = threadIdx.x & 31;
+    const ChunkScalars sc = chunk_scalars(m, c, 256, 1);
+    const uint32_t bits = (__ldg(m.rowend + ((c * 256) >> 5) + (lane >> 2)) >> ((lane & 3) * 8)) & 0xFFu;
+    int col[8];
+    double a[8];
+    load_unit<K, R>(m, c * 32 + lane, col, a);
+    double xv[8];
+#pragma unroll
+    for (int i = 0; i < 8; i++) xv[i] = __ldg(x + col_of(m, col[i]));
+    const int cnt = __popc(bits);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const int excl = incl - cnt;
+    const int total_ends = __shfl_sync(FULL, incl, 31);
+    double cur = 0.0, hp = 0.0, dot = 0.0;
+    int j = 0;
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        cur = fma(a[i], xv[i], cur);
+        const bool end = (bits >> i) & 1u;
+        if (end && j > 0) {         // a row that starts and ends in this lane: ordinal excl + j >= 1
+            const int64_t Rw = actual_row(m, sc.row0 + excl + j);
+            if (DOT) dot = fma(__ldg(e.p + Rw), cur, dot);
+            epi_finish_t<RESID>(e, Rw, cur);
+        }
+        hp = end && j == 0 ? cur : hp;
+        j += end ? 1 : 0;
+        cur = end ? 0.0 : cur;
+    }
+    const bool seen = j > 0;
+    double out = cur;
+    if (!__all_sync(FULL, seen)) {  // rows crossing lanes: segmented scan of the lane carries
+        double v = cur;
+        bool f = seen;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const double vu = __shfl_up_sync(FULL, v, o);
+            const bool fu = __shfl_up_sync(FULL, (int)f, o) != 0;
+            if (lane >= o) {
+                if (!f) v += vu;
+                f = f || fu;
+            }
+        }
+        out = v;
+    }
+    double in = __shfl_up_sync(FULL, out, 1);
+    if (lane == 0) in = 0.0;
+    if (seen) {                     // the lane's first row end: ordinal excl
+        const double v = in + hp;
+        if (excl == 0 && sc.starts_mid) {
+            if (DOT) dot = fma(__ldg(e.p + actual_row(m, sc.row0)), v, dot);
+            m.part[c] = v;
+        } else {
+            const int64_t Rw = actual_row(m, sc.row0 + excl);
+            if (DOT) dot = fma(__ldg(e.p + Rw), v, dot);
+            epi_finish_t<RESID>(e, Rw, v);
+        }
+    }
+    const double out31 = __shfl_sync(FULL, out, 31);
+    const bool last_end = __shfl_sync(FULL, (bits >> 7) & 1u, 31) != 0;
+    if (lane == 0) {
+        if (total_ends == 0) {
+            if (sc.row0 < m.n_nonempty) {
+                if (DOT) dot = fma(__ldg(e.p + actual_row(m, sc.row0)), out31, dot);
+                if (sc.starts_mid) m.part[c] = out31;
+                else m.carry[c] = out31;
+            }
+        } else {
+            const int64_t ro = sc.row0 + total_ends;
+            if (!last_end && ro < m.n_nonempty) {
+                if (DOT) dot = fma(__ldg(e.p + actual_row(m, ro)), out31, dot);
+                m.carry[c] = out31;
+            }
+        }
+    }
+    return dot;
+}
+
+// Warps w0, w0 + wstride, ... of a launch take chunks w0, w0 + wstride, ...
+template <int K, int R, bool DOT, bool RESID>
+__device__ __forceinline__ double spmv_chunks_direct(const MatView& m, const double* __restrict__ x, const Epi& e,
+                                                     int64_t w0, int64_t wstride, int64_t n_chunks) {
+    double dot = 0.0;
+    for (int64_t c = w0; c < n_chunks; c += wstride) dot += compute_chunk_direct<K, R, DOT, RESID>(m, e, c, x);
     return dot;
 }
 
