@@ -107,6 +107,29 @@ __device__ __forceinline__ double decode_l3_fast(uint32_t h, uint32_t t1, uint32
     return __hiloint2double((int)hi, (int)(uint32_t)low);
 }
 
+// Level 3 without a data-dependent branch, for W_3 <= 52 and s3 <= 23: the
+// leading one lies in the head, else in tail1, else in tail2; that segment's
+// FP32 image gives the exponent and its bits below the leading one, and the
+// segments after it are shifted in right below.  Bit-identical to decode_l3
+// for every value (zero and, via the group test Eg <= W_3, subnormal results
+// included).
+__device__ __forceinline__ double decode_l3_sel(uint32_t h, uint32_t t1, uint32_t t2, int Eg, const MatView& m) {
+    const uint32_t mag = h & ((1u << m.W1) - 1u);
+    if (Eg <= m.W3) return decode_l3(h, t1, t2, Eg, m);          // results may be subnormal: exact path
+    const bool in_h = mag != 0, in_1 = t1 != 0;
+    const uint32_t lead = in_h ? mag : (in_1 ? t1 : t2);
+    const int base = in_h ? m.s2 + m.s3 : (in_1 ? m.s3 : 0);        // bit position of the lead segment in M_3
+    const uint64_t rest = in_h ? (((uint64_t)t1 << m.s3) | t2) : (in_1 ? (uint64_t)t2 : 0ull);
+    const uint32_t fb = __float_as_uint(__uint_as_float(0x4B000000u | lead) - 8388608.0f);
+    // leading one of M_3 at bit base + p, p = (fb >> 23) - 127; the rest goes to
+    // the mantissa bits below 52 - p, i.e. rest << (52 - base - p)
+    const uint64_t low = rest << (((179 - base) - (int)(fb >> 23)) & 63);   // in 1..52 whenever lead != 0
+    const uint32_t hi = ((fb >> 3) + ((uint32_t)(Eg - m.W3 - 127 + base) << 20)) | ((h >> m.W1) << 31) |
+                        (uint32_t)(low >> 32);
+    const uint32_t sign = (h >> m.W1) << 31;
+    return lead ? __hiloint2double((int)hi, (int)(uint32_t)low) : __hiloint2double((int)sign, 0);
+}
+
 // FP32 -> FP64 widening with integer operations (exact; no FP64 pipe use).
 __device__ __forceinline__ double widen_f32(uint32_t f) {
     const uint32_t sign = f & 0x80000000u;
@@ -212,7 +235,7 @@ __device__ __forceinline__ void load_unit(const MatView& m, int64_t u, int* col,
                         t2 = (t2 << m.r_lo) | ((lo[bit >> 5] >> (bit & 31)) & ((1u << m.r_lo) - 1u));
                     }
                 }
-                if ((R == 0 || R == 4) && ok_l3_fast(h, Eg, m)) a[i] = decode_l3_fast(h, u16_of(t1w, i), t2, Eg, m);
+                if constexpr (R == 0 || R == 4) a[i] = decode_l3_sel(h, u16_of(t1w, i), t2, Eg, m);
                 else a[i] = decode_l3(h, u16_of(t1w, i), t2, Eg, m);
             }
         }

@@ -188,7 +188,12 @@ __device__ __forceinline__ double row_value(const MatView& m, const RowStage& L,
             const int bit = i * r;
             t2 = (t2 << r) | ((lw[bit >> 5] >> (bit & 31)) & ((1u << r) - 1u));
         }
-        if ((R == 0 || R == 4) && ok_l3_fast(h, Eg, m)) return decode_l3_fast(h, t1, t2, Eg, m);
+        if constexpr (R == 0 || R == 4) {
+            // the row schedule serves matrices whose groups rarely hold values
+            // 2^15 below their maximum: the head-only form, else the general one
+            if (ok_l3_fast(h, Eg, m)) return decode_l3_fast(h, t1, t2, Eg, m);
+            return decode_l3_sel(h, t1, t2, Eg, m);
+        }
         return decode_l3(h, t1, t2, Eg, m);
     }
 }
@@ -445,7 +450,8 @@ __device__ __forceinline__ void unit_values_blk(const MatView& m, const ChunkSta
                     const int bit = i * r;
                     t2 = (t2 << r) | ((lo[bit >> 5] >> (bit & 31)) & ((1u << r) - 1u));
                 }
-                a[i] = decode_l3(h, u16_of(t1w, i), t2, Eg, m);
+                if constexpr (R == 0 || R == 4) a[i] = decode_l3_sel(h, u16_of(t1w, i), t2, Eg, m);
+                else a[i] = decode_l3(h, u16_of(t1w, i), t2, Eg, m);
             }
         }
     }
