@@ -205,6 +205,8 @@ def main():
                     help="no timing: FP64 GMRES(30) for ITERS iterations on the N^2 convection-diffusion "
                          "operator and exit; the target for ncu captures of the GMRES kernels")
     ap.add_argument("--serve-requests", type=int, default=1000)
+    ap.add_argument("--serve-rates", default="0.5,1,2",
+                    help="arrival rates as fractions of the measured saturated batch throughput")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -436,8 +438,9 @@ def main():
         if not args.no_batch:
             batched = batched_comparison(gse, torch, args.batch_systems, rank, world)
         if not args.no_serve:
-            rate = 0.5 * batched["gse_stepped_batched"]["solves_per_s"] if batched else 200.0
-            served = served_benchmark(gse, torch, args.serve_requests, rate, rank, world)
+            rate = batched["gse_stepped_batched"]["solves_per_s"] if batched else 400.0
+            factors = tuple(float(f) for f in args.serve_rates.split(","))
+            served = served_benchmark(gse, torch, args.serve_requests, rate, rank, world, factors)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -607,16 +610,41 @@ def batched_comparison(gse, torch, nsys, rank, world):
     return out
 
 
-def served_benchmark(gse, torch, nreq, rate, rank, world):
+def served_benchmark(gse, torch, nreq, rate, rank, world, rate_factors=(0.5,)):
     """Poisson arrivals of nreq solve requests drawn from the batched
     distribution (a pool of 64 systems), admitted by HBM footprint into a
-    continuous batch; p50/p99 latency from arrival to completion."""
+    continuous batch; p50/p99 latency from arrival to completion.  One run per
+    arrival rate factor (times the saturated batch throughput `rate`); the
+    first factor's run is reported at the top level, all of them in `sweep`."""
     from paper_2411_04686_gb300 import serve
     specs = synth.batch_specs(64, seed=1)
     pool = []
     for sp in specs:
         A = sp.build()
         pool.append((A, synth.rhs_ones(A)))
+    sweep = []
+    for f in rate_factors:
+        sweep.append(_served_run(gse, serve, pool, nreq, rate * f, rank, world))
+        sweep[-1]["rate_factor"] = f
+    out = dict(sweep[0])
+    out["sweep"] = sweep
+    # one-at-a-time FP64 CSR CG throughput on the same pool (8 systems)
+    t_single = 0.0
+    for A, b in pool[:8]:
+        M = gse.GseMatrix.from_csr(A, attach=(64,))
+        bd = torch.from_numpy(b).cuda()
+        x = torch.zeros(A.n_rows, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        M.cg(bd, x, tol=1e-10, policy=gse.fp64_policy(gse.SCALED_CG))
+        torch.cuda.synchronize()
+        t_single += time.perf_counter() - t1
+        M.free()
+    out["fp64_one_at_a_time_solves_per_s"] = round(8 / t_single, 2)
+    return out
+
+
+def _served_run(gse, serve, pool, nreq, rate, rank, world):
     arrivals = serve.poisson_arrivals(nreq, rate, seed=2)
     rng = np.random.default_rng(3)
     picks = rng.integers(0, len(pool), nreq)
@@ -641,22 +669,9 @@ def served_benchmark(gse, torch, nreq, rate, rank, world):
     srv.close()
     st = serve.latency_stats(srv.done)
     ok = all(c.info["status"] == gse.OK for c in srv.done)
-    # one-at-a-time FP64 CSR CG throughput on the same pool (8 systems)
-    t_single = 0.0
-    for A, b in pool[:8]:
-        M = gse.GseMatrix.from_csr(A, attach=(64,))
-        bd = torch.from_numpy(b).cuda()
-        x = torch.zeros(A.n_rows, dtype=torch.float64, device="cuda")
-        torch.cuda.synchronize()
-        t1 = time.perf_counter()
-        M.cg(bd, x, tol=1e-10, policy=gse.fp64_policy(gse.SCALED_CG))
-        torch.cuda.synchronize()
-        t_single += time.perf_counter() - t1
-        M.free()
     return {"requests": len(reqs), "arrival_rate_per_s": round(rate, 2), "wall_s": round(wall, 3),
             "solves_per_s": round(len(srv.done) / wall, 2), "p50_latency_s": round(st.get("p50_s", 0), 4),
-            "p99_latency_s": round(st.get("p99_s", 0), 4), "all_converged": ok,
-            "fp64_one_at_a_time_solves_per_s": round(8 / t_single, 2)}
+            "p99_latency_s": round(st.get("p99_s", 0), 4), "all_converged": ok}
 
 
 if __name__ == "__main__":

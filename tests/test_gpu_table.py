@@ -123,3 +123,25 @@ def test_table_rejects_bad_num_exp():
         with pytest.raises(gse.GseError) as e:
             gse.GseMatrix.from_csr(A, num_exp=ne)
         assert e.value.code == gse.ERR_INVALID
+
+
+def test_batch_mixing_formats_and_schedules_equals_solo_bitwise():
+    """One engine launch mixing per-group and table-format systems on both
+    schedules (row and nonzero split) gives each system its solo result."""
+    As = [s.build() for s in synth.batch_specs(9, seed=9, n_lo=300, n_hi=15000)]
+    mats = []
+    for i, A in enumerate(As):
+        M = gse.GseMatrix.from_csr(A, num_exp=8 if i % 2 else 0)
+        if i % 3 == 0:
+            M.set_schedule(1)               # nonzero split in the engine
+        mats.append(M)
+    bs = [torch.from_numpy(synth.rhs_ones(A)).cuda() for A in As]
+    xs = [torch.zeros(A.n_rows, dtype=torch.float64, device="cuda") for A in As]
+    rc, infos = gse.batch_cg(mats, bs, xs)
+    assert rc == gse.OK
+    for M, A, b, xb, ib in zip(mats, As, bs, xs, infos):
+        x1 = torch.zeros(A.n_rows, dtype=torch.float64, device="cuda")
+        i1 = M.cg(b, x1)
+        assert ib["status"] == gse.OK and ib["rel_res_true"] < 1e-10
+        assert ib["iters"] == i1["iters"] and ib["switch_iter"] == i1["switch_iter"]
+        assert torch.equal(xb, x1)
