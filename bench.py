@@ -309,6 +309,8 @@ def main():
             for i, t in enumerate(ts):
                 per_launch[i].append(t)
         torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
         wall = time.perf_counter() - t0
     clocks = clk.summary()
     kernel_ms = [sum(v) / len(v) for v in per_launch]
@@ -588,7 +590,15 @@ def batched_comparison(gse, torch, nsys, rank, world):
         rc, infos = gse.batch_cg(mats, bs, xs, tol=1e-10, policy=pol)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        out[name] = {"seconds": round(dt, 4), "solves_per_s": round(len(As) / dt, 2), "status": rc,
+        nsolved = len(As)
+        if world > 1:                    # whole job: all ranks' systems over the slowest rank's time
+            import torch.distributed as tdist
+            t = torch.tensor([dt, float(len(As))], device="cuda", dtype=torch.float64)
+            tm = t[:1].clone()
+            tdist.all_reduce(tm, op=tdist.ReduceOp.MAX)
+            tdist.all_reduce(t[1:], op=tdist.ReduceOp.SUM)
+            dt, nsolved = float(tm.item()), int(t[1].item())
+        out[name] = {"seconds": round(dt, 4), "solves_per_s": round(nsolved / dt, 2), "status": rc,
                      "all_converged": all(i["status"] == gse.OK for i in infos),
                      "max_iters": max(i["iters"] for i in infos),
                      "max_rel_res_true": max(i["rel_res_true"] for i in infos)}
