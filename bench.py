@@ -593,11 +593,11 @@ def batched_comparison(gse, torch, nsys, rank, world):
         nsolved = len(As)
         if world > 1:                    # whole job: all ranks' systems over the slowest rank's time
             import torch.distributed as tdist
-            t = torch.tensor([dt, float(len(As))], device="cuda", dtype=torch.float64)
-            tm = t[:1].clone()
+            tm = torch.tensor([dt], device="cuda", dtype=torch.float64)
+            tn = torch.tensor([float(len(As))], device="cuda", dtype=torch.float64)
             tdist.all_reduce(tm, op=tdist.ReduceOp.MAX)
-            tdist.all_reduce(t[1:], op=tdist.ReduceOp.SUM)
-            dt, nsolved = float(tm.item()), int(t[1].item())
+            tdist.all_reduce(tn, op=tdist.ReduceOp.SUM)
+            dt, nsolved = float(tm.item()), int(tn.item())
         out[name] = {"seconds": round(dt, 4), "solves_per_s": round(nsolved / dt, 2), "status": rc,
                      "all_converged": all(i["status"] == gse.OK for i in infos),
                      "max_iters": max(i["iters"] for i in infos),
