@@ -608,7 +608,14 @@ struct EngineSlot {
 
 struct gse_cg_engine {
     int capacity = 0;
-    cudaStream_t stream = nullptr;
+    cudaStream_t user = nullptr;    // the caller's stream: each call starts after its work and ends before its next
+    cudaStream_t stream = nullptr;  // the engine's own stream (capturable; all engine work runs here)
+    cudaEvent_t join = nullptr;
+    // a batch of iteration slots captured once as a CUDA graph and replayed
+    // (re-captured when the set of systems changes)
+    cudaGraphExec_t graph = nullptr;
+    int graph_slots = 0;
+    bool graph_ok = true;
     int device = 0;
     int num_sms = 1;
     SysDesc* d_sys = nullptr;
@@ -629,11 +636,28 @@ struct gse_cg_engine {
 };
 
 
+// The engine's stream waits for the caller's stream (its b and x are ready) ...
+static void engine_enter(gse_cg_engine* e) {
+    cudaEventRecord(e->join, e->user);
+    cudaStreamWaitEvent(e->stream, e->join, 0);
+}
+// ... and the caller's stream waits for the engine's work.
+static void engine_leave(gse_cg_engine* e) {
+    cudaEventRecord(e->join, e->stream);
+    cudaStreamWaitEvent(e->user, e->join, 0);
+}
+
 extern "C" int gse_engine_create(int capacity, void* stream, gse_engine* out) {
     if (capacity < 1 || !out) return GSE_ERR_INVALID;
     gse_cg_engine* e = new gse_cg_engine();
     e->capacity = capacity;
-    e->stream = (cudaStream_t)stream;
+    e->user = (cudaStream_t)stream;
+    if (cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&e->join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        delete e;
+        return GSE_ERR_CUDA;
+    }
     cudaGetDevice(&e->device);
     cudaDeviceGetAttribute(&e->num_sms, cudaDevAttrMultiProcessorCount, e->device);
     p1_occupancy(false, p1_smem());     // sets both kernels' shared-memory limits
@@ -658,7 +682,10 @@ extern "C" int gse_engine_create(int capacity, void* stream, gse_engine* out) {
 
 extern "C" void gse_engine_destroy(gse_engine e) {
     if (!e) return;
-    if (e->stream || true) cudaStreamSynchronize(e->stream);
+    cudaStreamSynchronize(e->stream);
+    if (e->graph) cudaGraphExecDestroy(e->graph);
+    cudaStreamDestroy(e->stream);
+    if (e->join) cudaEventDestroy(e->join);
     if (e->d_sys) cudaFree(e->d_sys);
     if (e->d_state) cudaFree(e->d_state);
     if (e->h_state) cudaFreeHost(e->h_state);
@@ -688,6 +715,7 @@ extern "C" int gse_engine_submit(gse_engine e, gse_handle h, const double* b, do
     for (int i = 0; i < e->capacity; i++)
         if (!e->slots[i].active && e->slots[i].done_reported) { slot = i; break; }
     if (slot < 0) return GSE_ERR_INVALID;
+    engine_enter(e);
     int rc = ensure_cg_workspace(h, e->stream);
     if (rc != GSE_OK) return rc;
     if ((pol->flags & GSE_POLICY_FLOOR) && !base) {
@@ -777,6 +805,10 @@ static int rebuild_maps(gse_cg_engine* e) {
     e->nblk_vec = (int)mv.size();
     e->rows_smem = rsm;
     e->dirty = false;
+    if (e->graph) {
+        cudaGraphExecDestroy(e->graph);
+        e->graph = nullptr;
+    }
     return GSE_OK;
 }
 
@@ -793,6 +825,38 @@ static void enqueue_slots(gse_cg_engine* e, int nslots) {
     }
 }
 
+// Runs nslots iteration slots: a full batch from the captured graph (captured
+// on first use), anything else launched directly.
+static void run_slots(gse_cg_engine* e, int nslots, int batch) {
+    if (nslots == batch && e->graph_ok) {
+        if (!e->graph || e->graph_slots != batch) {
+            if (e->graph) {
+                cudaGraphExecDestroy(e->graph);
+                e->graph = nullptr;
+            }
+            cudaGraph_t g = nullptr;
+            if (cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+                enqueue_slots(e, nslots);
+                if (cudaStreamEndCapture(e->stream, &g) == cudaSuccess && g &&
+                    cudaGraphInstantiate(&e->graph, g, 0) == cudaSuccess) {
+                    e->graph_slots = batch;
+                } else {
+                    e->graph = nullptr;
+                }
+                if (g) cudaGraphDestroy(g);
+            }
+            if (!e->graph) {             // capture unavailable: launch directly from now on
+                cudaGetLastError();
+                e->graph_ok = false;
+            }
+        }
+        if (e->graph && cudaGraphLaunch(e->graph, e->stream) == cudaSuccess) return;
+        cudaGetLastError();
+        e->graph_ok = false;
+    }
+    enqueue_slots(e, nslots);
+}
+
 static bool any_running(gse_cg_engine* e) {
     for (int i = 0; i < e->capacity; i++)
         if (e->slots[i].active && e->h_state[i].mode != MODE_DONE) return true;
@@ -804,6 +868,7 @@ static bool any_running(gse_cg_engine* e) {
 extern "C" int gse_engine_run(gse_engine e, int max_slots, int batch, int* n_running) {
     if (!e || max_slots < 0) return GSE_ERR_INVALID;
     if (batch < 1) batch = 8;
+    engine_enter(e);
     if (e->dirty) {
         const int rc = rebuild_maps(e);
         if (rc != GSE_OK) return rc;
@@ -822,7 +887,7 @@ extern "C" int gse_engine_run(gse_engine e, int max_slots, int batch, int* n_run
     bool running = true;
     while (done_slots < max_slots && running) {
         const int nb = max_slots - done_slots < batch ? max_slots - done_slots : batch;
-        enqueue_slots(e, nb);
+        run_slots(e, nb, batch);
         done_slots += nb;
         cudaMemcpyAsync(e->h_stage[cur], e->d_state, sbytes, cudaMemcpyDeviceToHost, e->stream);
         cudaEventRecord(e->ev[cur], e->stream);
@@ -836,6 +901,7 @@ extern "C" int gse_engine_run(gse_engine e, int max_slots, int batch, int* n_run
         cur ^= 1;
     }
     cudaStreamSynchronize(e->stream);
+    engine_leave(e);
     if (inflight) memcpy(e->h_state, e->h_stage[cur ^ 1], sbytes);
     running = any_running(e);
     if (cudaGetLastError() != cudaSuccess) return GSE_ERR_CUDA;
@@ -885,6 +951,7 @@ static double true_residual(gse_cg_engine* e, int slot) {
 // Reports finished systems (slots and infos, up to max_done) and frees their slots.
 extern "C" int gse_engine_poll(gse_engine e, int* done_slots, gse_solve_info* infos, int max_done, int* n_done) {
     if (!e) return GSE_ERR_INVALID;
+    engine_enter(e);
     int c = 0;
     for (int i = 0; i < e->capacity && c < max_done; i++) {
         EngineSlot& sl = e->slots[i];
@@ -910,6 +977,7 @@ extern "C" int gse_engine_poll(gse_engine e, int* done_slots, gse_solve_info* in
 // Cancels a slot (its system stays where it is; info reports MAXITER).
 extern "C" int gse_engine_cancel(gse_engine e, int slot, gse_solve_info* info) {
     if (!e || slot < 0 || slot >= e->capacity || !e->slots[slot].active) return GSE_ERR_INVALID;
+    engine_enter(e);
     cudaStreamSynchronize(e->stream);
     cudaMemcpy(&e->h_state[slot], e->d_state + slot, sizeof(CgState), cudaMemcpyDeviceToHost);
     if (info) fill_info(e, slot, info, true_residual(e, slot));
