@@ -88,6 +88,9 @@ def lib():
         L.orc_widen16.argtypes = [_I64, _P, _I, _P]
         L.orc_table_encode.argtypes = [_I64, _P, _P, _I, _P, _I, _P, _P, _P, _P]
         L.orc_table_decode.argtypes = [_I64, _P, _P, _P, _P, _P, _I, _P, _I, _I, _P]
+        L.orc_table_build_sampled.argtypes = [_I64, _P, _P, _I, _I64, _P, _P]
+        L.orc_table_encode_in_value.argtypes = [_I64, _P, _P, _I, _P, _I, _P, _P, _P]
+        L.orc_table_decode_in_value.argtypes = [_I64, _P, _P, _P, _P, _I, _P, _I, _I, _P]
         L.orc_spmv.argtypes = [_I64, _P, _P, _P, _P, _P]
         L.orc_spmv.restype = None
         L.orc_gse_spmv.argtypes = [_I64, _P, _P, _P, _P, _P, _P, _I, _P, _I, _I, _P, _P]
@@ -192,9 +195,63 @@ def table_decode(head, tail1, tail2, idx, table, k, seg_bits=(16, 16, 20)):
     return out
 
 
-def table_levels(val, num_exp, seg_bits=(16, 16, 20)):
-    """(table, [A_1 .. A_nseg values]) of the table format."""
-    table = table_build(val, num_exp)
+def table_build_sampled(row_ptr, val, num_exp, block_rows, sample_rows):
+    """The table from the sampled extraction of Sec. III-B: the exponents of
+    row sample_rows[b] stand for the block of block_rows rows b belongs to."""
+    row_ptr, val = _c(row_ptr, np.int32), _c(val, np.float64)
+    sample_rows = _c(sample_rows, np.int64)
+    n_rows = row_ptr.size - 1
+    if sample_rows.size != (n_rows + block_rows - 1) // block_rows:
+        raise ValueError("one sample row per block")
+    table = np.zeros(max(num_exp, 1), np.int16)
+    n = lib().orc_table_build_sampled(n_rows, _ptr(row_ptr), _ptr(val), num_exp, block_rows, _ptr(sample_rows),
+                                      _ptr(table))
+    if n < 1:
+        raise ValueError(f"orc_table_build_sampled status {n}")
+    return table[:n].copy()
+
+
+def table_encode_in_value(val, table, seg_bits=(16, 16, 20)):
+    """The table format with the index in the top head bits (Sec. III-C's
+    layout for column counts without spare bits): (head u16, tail1 u16, tail2 u32)."""
+    val, table = _c(val, np.float64), _c(table, np.int16)
+    nnz = val.size
+    sb, nseg = _segs(seg_bits)
+    head = np.zeros(nnz, np.uint16)
+    t1 = np.zeros(nnz, np.uint16)
+    t2 = np.zeros(nnz, np.uint32)
+    rc = lib().orc_table_encode_in_value(nnz, _ptr(val), _ptr(table), table.size, _ptr(sb), nseg, _ptr(head),
+                                         _ptr(t1), _ptr(t2))
+    if rc != 0:
+        raise ValueError(f"orc_table_encode_in_value status {rc}")
+    return head, t1, t2
+
+
+def table_decode_in_value(head, tail1, tail2, table, k, seg_bits=(16, 16, 20)):
+    head, tail1 = _c(head, np.uint16), _c(tail1, np.uint16)
+    tail2, table = _c(tail2, np.uint32), _c(table, np.int16)
+    sb, nseg = _segs(seg_bits)
+    out = np.zeros(head.size, np.float64)
+    rc = lib().orc_table_decode_in_value(head.size, _ptr(head), _ptr(tail1), _ptr(tail2), _ptr(table), table.size,
+                                         _ptr(sb), nseg, k, _ptr(out))
+    if rc != 0:
+        raise ValueError(f"orc_table_decode_in_value status {rc}")
+    return out
+
+
+def index_bits(n_table):
+    """Bits an exponent index takes for a table of n_table entries."""
+    return max(int(n_table) - 1, 0).bit_length()
+
+
+def table_levels(val, num_exp, seg_bits=(16, 16, 20), table=None, index_in_value=False):
+    """(table, [A_1 .. A_nseg values]) of the table format; the table is built
+    from all values unless given; index_in_value selects the head layout."""
+    if table is None:
+        table = table_build(val, num_exp)
+    if index_in_value:
+        enc = table_encode_in_value(val, table, seg_bits)
+        return table, [table_decode_in_value(*enc, table, k, seg_bits) for k in range(1, len(seg_bits) + 1)]
     enc = table_encode(val, table, seg_bits)
     return table, [table_decode(*enc, table, k, seg_bits) for k in range(1, len(seg_bits) + 1)]
 

@@ -31,6 +31,9 @@
  * index per nonzero (Sec. III-C keeps it in the column index's top bits); a
  * value whose exponent plus 1 is not in the table is denormalized against the
  * nearest larger entry (Alg. 1).  The segment split is the same.
+ * orc_table_build_sampled is the sampled extraction of Sec. III-B (one random
+ * row per row block); orc_table_*_in_value keep the index in the top head bits
+ * instead (Sec. III-C, for column counts without spare bits).
  *
  * 16-bit baselines: orc_round16 / orc_widen16 store the values as FP16 or
  * BF16 (round to nearest even, one rounding from FP64) for the baseline SpMV
@@ -177,6 +180,24 @@ int orc_decode(int64_t nnz, const uint16_t* head, const uint16_t* tail1, const u
  * matrix without a normal value gets the single entry 0.  Returns -ORC_NONFINITE
  * when a value is Inf or NaN, ORC_ERR_INVALID for bad arguments.
  */
+static int select_entries(const int64_t* count, int emax, int num_exp, int16_t* table)
+{
+    int n = 0;
+    int taken[2048] = {0};
+    while (n < num_exp) {                 /* selection by (count desc, exponent desc) */
+        int best = -1;
+        for (int e = 2046; e >= 1; e--)
+            if (count[e] > 0 && !taken[e] && (best < 0 || count[e] > count[best])) best = e;
+        if (best < 0) break;
+        taken[best] = 1;
+        table[n++] = (int16_t)(best + 1);
+    }
+    if (n == 0) table[n++] = (int16_t)(emax + 1);   /* nothing counted: max + 1 alone */
+    else if (!taken[emax]) table[n - 1] = (int16_t)(emax + 1);
+    return n;
+}
+
+/* The exact extraction: every nonzero counted once. */
 int orc_table_build(int64_t nnz, const double* val, int num_exp, int16_t* table)
 {
     if (num_exp < 1 || nnz < 0) return ORC_ERR_INVALID;
@@ -190,17 +211,52 @@ int orc_table_build(int64_t nnz, const double* val, int num_exp, int16_t* table)
         if (e > emax) emax = e;
     }
     if (emax == 0) { table[0] = 0; free(count); return 1; }
-    int n = 0;
-    int taken[2048] = {0};
-    while (n < num_exp) {                 /* selection by (count desc, exponent desc) */
-        int best = -1;
-        for (int e = 2046; e >= 1; e--)
-            if (count[e] > 0 && !taken[e] && (best < 0 || count[e] > count[best])) best = e;
-        if (best < 0) break;
-        taken[best] = 1;
-        table[n++] = (int16_t)(best + 1);
+    int n = select_entries(count, emax, num_exp, table);
+    free(count);
+    return n;
+}
+
+/*
+ * Sec. III-B, the sampled extraction: the rows are cut into blocks of
+ * block_rows consecutive rows (the last may be shorter) and the exponent
+ * distribution of one row per block, sample_rows[b] (drawn by the caller),
+ * stands for the distribution of the whole block.  Reading: every row of block
+ * b is taken to hold the sampled row's exponents, so each of that row's
+ * nonzeros counts rows_in_block(b) times.  The selection is then that of
+ * orc_table_build.  max(e) + 1 must stay in the table for the encoding to be
+ * able to hold every value (Sec. III-B, "Denormalized Representation"), so the
+ * maximum exponent is taken over all values, not over the sample.  Returns the
+ * number of entries, -ORC_NONFINITE on Inf/NaN, ORC_ERR_INVALID for bad
+ * arguments or a sample row outside its block.
+ */
+int orc_table_build_sampled(int64_t n_rows, const int32_t* row_ptr, const double* val, int num_exp,
+                            int64_t block_rows, const int64_t* sample_rows, int16_t* table)
+{
+    if (num_exp < 1 || n_rows < 0 || block_rows < 1) return ORC_ERR_INVALID;
+    int64_t nnz = n_rows > 0 ? row_ptr[n_rows] : 0;
+    int emax = 0;
+    for (int64_t i = 0; i < nnz; i++) {
+        int e = (int)((bits_of(val[i]) >> 52) & 0x7FF);
+        if (e == 0x7FF) return -ORC_NONFINITE;
+        if (e > emax) emax = e;
     }
-    if (!taken[emax]) table[n - 1] = (int16_t)(emax + 1);
+    int64_t n_blocks = (n_rows + block_rows - 1) / block_rows;
+    for (int64_t b = 0; b < n_blocks; b++)
+        if (sample_rows[b] < b * block_rows || sample_rows[b] >= b * block_rows + block_rows ||
+            sample_rows[b] >= n_rows)
+            return ORC_ERR_INVALID;
+    if (emax == 0) { table[0] = 0; return 1; }
+    int64_t* count = calloc(2048, sizeof(int64_t));
+    for (int64_t b = 0; b < n_blocks; b++) {
+        int64_t first = b * block_rows;
+        int64_t rows_in_block = first + block_rows <= n_rows ? block_rows : n_rows - first;
+        int64_t r = sample_rows[b];
+        for (int64_t j = row_ptr[r]; j < row_ptr[r + 1]; j++) {
+            int e = (int)((bits_of(val[j]) >> 52) & 0x7FF);
+            if (e != 0) count[e] += rows_in_block;
+        }
+    }
+    int n = select_entries(count, emax, num_exp, table);
     free(count);
     return n;
 }
@@ -269,6 +325,65 @@ int orc_table_decode(int64_t nnz, const uint16_t* head, const uint16_t* tail1, c
     for (int64_t i = 0; i < nnz; i++) {
         if (idx[i] >= n_table) return ORC_ERR_INVALID;
         out[i] = decode_one(head[i], k >= 2 ? tail1[i] : 0, k >= 3 ? tail2[i] : 0, table[idx[i]], seg_bits, k);
+    }
+    return ORC_OK;
+}
+
+/*
+ * Sec. III-C, the index kept in the value array instead of the column index
+ * (for matrices whose column count leaves no spare bits).  Reading: the
+ * ceil(log2(n_table)) index bits b take the top magnitude bits of the head,
+ * right below the sign, so every level has b magnitude bits fewer:
+ *   head = sign << (s1 - 1) | index << (s1 - 1 - b) | M >> (W' - W'_1),
+ * where M is the Alg. 1 mantissa for the widths {s1 - b, s2, s3}, i.e. the
+ * segment split of orc_table_encode with a head of s1 - b bits whose sign is
+ * then moved up past the index.  Requires b <= s1 - 2.
+ */
+static int index_bits(int n_table)
+{
+    int b = 0;
+    while ((1 << b) < n_table) b++;
+    return b;
+}
+
+int orc_table_encode_in_value(int64_t nnz, const double* val, const int16_t* table, int n_table,
+                              const int* seg_bits, int nseg, uint16_t* head, uint16_t* tail1, uint32_t* tail2)
+{
+    if (total_width(seg_bits, nseg) < 0 || n_table < 1 || nnz < 0) return ORC_ERR_INVALID;
+    int b = index_bits(n_table);
+    if (b > seg_bits[0] - 2) return ORC_ERR_INVALID;
+    int short_bits[3] = {seg_bits[0] - b, nseg >= 2 ? seg_bits[1] : 0, nseg >= 3 ? seg_bits[2] : 0};
+    uint8_t* idx = malloc(nnz > 0 ? (size_t)nnz : 1);
+    int rc = orc_table_encode(nnz, val, table, n_table, short_bits, nseg, head, tail1, tail2, idx);
+    if (rc == ORC_OK) {
+        int ws = short_bits[0] - 1;                     /* magnitude bits left in the head */
+        for (int64_t i = 0; i < nnz; i++) {
+            uint32_t sign = (head[i] >> ws) & 1u;
+            uint32_t mag = head[i] & ((1u << ws) - 1u);
+            head[i] = (uint16_t)((sign << (seg_bits[0] - 1)) | ((uint32_t)idx[i] << ws) | mag);
+        }
+    }
+    free(idx);
+    return rc;
+}
+
+/* Decode of that layout at level k: the index and the short head are taken
+ * apart again and decoded as the table format with the widths {s1 - b, s2, s3}. */
+int orc_table_decode_in_value(int64_t nnz, const uint16_t* head, const uint16_t* tail1, const uint32_t* tail2,
+                              const int16_t* table, int n_table, const int* seg_bits, int nseg, int k, double* out)
+{
+    if (total_width(seg_bits, nseg) < 0 || k < 1 || k > nseg || n_table < 1) return ORC_ERR_INVALID;
+    int b = index_bits(n_table);
+    if (b > seg_bits[0] - 2) return ORC_ERR_INVALID;
+    int short_bits[3] = {seg_bits[0] - b, nseg >= 2 ? seg_bits[1] : 0, nseg >= 3 ? seg_bits[2] : 0};
+    int ws = short_bits[0] - 1;
+    for (int64_t i = 0; i < nnz; i++) {
+        uint32_t sign = (head[i] >> (seg_bits[0] - 1)) & 1u;
+        uint32_t ix = (head[i] >> ws) & ((1u << b) - 1u);
+        uint32_t mag = head[i] & ((1u << ws) - 1u);
+        if ((int)ix >= n_table) return ORC_ERR_INVALID;
+        uint16_t h = (uint16_t)((sign << ws) | mag);
+        out[i] = decode_one(h, k >= 2 ? tail1[i] : 0, k >= 3 ? tail2[i] : 0, table[ix], short_bits, k);
     }
     return ORC_OK;
 }
