@@ -106,6 +106,9 @@ typedef struct {
     int64_t overflow16;           /* finite values that became infinite when FP16
                                      values were attached (the paper's FP16
                                      arithmetic overflow); 0 otherwise            */
+    int index_in_head;            /* table format: 1 when the exponent index sits
+                                     in the head (GSE_INDEX_VALUE), 0 when it sits
+                                     in the column index or there is no table     */
 } gse_matrix_info;
 
 /* Error name for a status code (static string). */
@@ -240,17 +243,53 @@ int gse_export(gse_handle h, uint16_t* head, uint16_t* tail1, uint32_t* tail2, i
  *           nearest larger entry T (d = T - e);
  *   M = floor(|v| * 2^(W - (T - 1023))), split into head / tail1 / tail2 as in
  *           gse_encode (zeros and subnormals: M = 0, index 0).
- * num_exp in [1, 64].  The index takes ceil(log2(entries)) bits, so n_cols must
- * not exceed 2^(32 - bits) (GSE_ERR_UNSUPPORTED).  Every other call (SpMV at
- * any level, baselines, solvers, decode, footprint) accepts the handle.
- * Errors as gse_encode.
+ * num_exp in [1, 64].  The index takes b = ceil(log2(entries)) bits.  It goes
+ * in the column index while n_cols <= 2^(32 - b); otherwise, as Sec. III-C
+ * allows, into the value (GSE_INDEX_VALUE of gse_encode_table_ex).  Every other
+ * call (SpMV at any level, baselines, solvers, decode, footprint) accepts the
+ * handle.  Errors as gse_encode.
  */
 int gse_encode_table(const gse_csr* csr, int num_exp, const int* seg_bits, int n_seg, void* stream,
                      gse_handle* out);
 
+/* Where the exponent index of a table-format nonzero is kept. */
+#define GSE_INDEX_AUTO   0   /* column index if its spare bits hold it, else the head */
+#define GSE_INDEX_COL    1   /* top b bits of the column index (Sec. III-C, Alg. 2);
+                                GSE_ERR_UNSUPPORTED when n_cols > 2^(32 - b)       */
+#define GSE_INDEX_VALUE  2   /* the b head bits right below the sign (Sec. III-C,
+                                for column counts without spare bits): every level
+                                keeps b magnitude bits fewer, W_k' = W_k - b, and
+                                M = floor(|v| * 2^(W' - (T - 1023)));
+                                head = sign << (s1-1) | index << (s1-1-b) |
+                                top s1-1-b bits of M.  Needs b <= s1 - 2
+                                (GSE_ERR_UNSUPPORTED otherwise).                   */
+
+/*
+ * gse_encode_table with the placement of the index and, optionally, the
+ * sampled exponent extraction of Sec. III-B.
+ *   index_place: GSE_INDEX_AUTO / GSE_INDEX_COL / GSE_INDEX_VALUE.
+ *   block_rows:  0 counts every nonzero (the exact extraction).  > 0 cuts the
+ *                rows into blocks of block_rows rows (the last may be shorter)
+ *                and counts only the nonzeros of one row per block,
+ *                sample_rows[b] (host array of ceil(n_rows / block_rows)
+ *                row indices, each inside its block; the caller draws them).
+ *                Each counts as many times as its block has rows.  The entries
+ *                are then chosen from these counts as in gse_encode_table.
+ *                max exponent + 1 is still taken over all values, so every
+ *                value has an entry at or above its exponent.
+ * Errors: GSE_ERR_INVALID (as gse_encode; num_exp outside [1, 64]; a bad
+ * index_place; block_rows < 0; a sample row outside its block or NULL
+ * sample_rows), GSE_ERR_UNSUPPORTED (the chosen place cannot hold the index),
+ * GSE_ERR_NONFINITE, GSE_ERR_OOM.  sample_rows is read before the call returns.
+ */
+int gse_encode_table_ex(const gse_csr* csr, int num_exp, const int* seg_bits, int n_seg, int index_place,
+                        int64_t block_rows, const int64_t* sample_rows, void* stream, gse_handle* out);
+
 /* Table-format handle (tests): the table (at most 64 int16 entries, host),
- * its entry count, and the index of every nonzero (idx[nnz], host).  Any
- * pointer may be NULL.  GSE_ERR_INVALID for a per-group handle. */
+ * its entry count, and the index of every nonzero (idx[nnz], host; read from
+ * the column words or the heads, wherever it is kept).  Any pointer may be
+ * NULL.  GSE_ERR_INVALID for a per-group handle.  gse_export returns the heads
+ * as stored, index bits included. */
 int gse_export_table(gse_handle h, int16_t* table, int* n_table, uint8_t* idx);
 
 /* vals[nnz] (device) = the FP64 values of A_k in CSR order (tests). */

@@ -21,13 +21,14 @@ ERR_INVALID, ERR_NONFINITE, ERR_OOM, ERR_CUDA, ERR_UNSUPPORTED = -1, -2, -3, -4,
 LEVEL_FP64, LEVEL_FP32, LEVEL_FP16, LEVEL_BF16 = 64, 32, 16, 17
 POLICY_NO_STAGNATION, POLICY_FLOOR = 1, 2
 SCHEDULE_ROWS = 8
+INDEX_AUTO, INDEX_COL, INDEX_VALUE = 0, 1, 2
 
 # every symbol include/gse.h declares
 EXPORTS = ["gse_strerror", "gse_encode", "gse_attach_values", "gse_spmv", "gse_cg", "gse_cg_noalloc", "gse_gmres",
            "gse_batch_cg", "gse_engine_create", "gse_engine_submit", "gse_engine_run",
            "gse_engine_poll", "gse_engine_cancel", "gse_engine_destroy", "gse_export", "gse_decode",
            "gse_matrix_get_info", "gse_set_schedule", "gse_autotune", "gse_footprint",
-           "gse_solve_footprint", "gse_free", "gse_encode_table", "gse_export_table"]
+           "gse_solve_footprint", "gse_free", "gse_encode_table", "gse_encode_table_ex", "gse_export_table"]
 
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -66,7 +67,8 @@ class MatrixInfo(ctypes.Structure):
     _fields_ = [("n_rows", _I64), ("n_cols", _I64), ("nnz", _I64), ("n_groups", _I64),
                 ("n_empty_rows", _I64), ("group_size", _I), ("n_seg", _I), ("seg_bits", _I * 3),
                 ("max_row_len", _I), ("mean_row_len", _D), ("schedule", _I),
-                ("bytes_level", _I64 * 3), ("num_exp", _I), ("overflow16", _I64)]
+                ("bytes_level", _I64 * 3), ("num_exp", _I), ("overflow16", _I64),
+                ("index_in_head", _I)]
 
 
 _lib = None
@@ -89,6 +91,7 @@ def lib():
     L.gse_strerror.argtypes = [_I]
     L.gse_encode.argtypes = [ctypes.POINTER(CSR), _I, _P, _I, _P, ctypes.POINTER(_P)]
     L.gse_encode_table.argtypes = [ctypes.POINTER(CSR), _I, _P, _I, _P, ctypes.POINTER(_P)]
+    L.gse_encode_table_ex.argtypes = [ctypes.POINTER(CSR), _I, _P, _I, _I, _I64, _P, _P, ctypes.POINTER(_P)]
     L.gse_export_table.argtypes = [_P, _P, _P, _P]
     L.gse_attach_values.argtypes = [_P, ctypes.POINTER(CSR), _I, _P]
     L.gse_spmv.argtypes = [_P, _I, _P, _P, _P]
@@ -180,7 +183,8 @@ class GseMatrix:
     """An encoded matrix on the current CUDA device (owns a gse_handle)."""
 
     def __init__(self, row_ptr, col, val, n_cols=None, group_size=32, seg_bits=(16, 16, 20),
-                 stream=None, attach=(), num_exp=0):
+                 stream=None, attach=(), num_exp=0, index_place=INDEX_AUTO, sample_block_rows=0,
+                 sample_rows=None):
         import torch
         L = lib()
         self._keep = []
@@ -204,9 +208,16 @@ class GseMatrix:
         sb = (ctypes.c_int * 3)(*(list(seg_bits) + [0] * (3 - len(seg_bits))))
         h = ctypes.c_void_p()
         self.stream = _stream_ptr(stream)
-        if num_exp:      # the paper's global exponent table (Sec. III-B), index in the column word
-            _check(L.gse_encode_table(ctypes.byref(self.csr), num_exp, ctypes.cast(sb, _P), len(seg_bits),
-                                      self.stream, ctypes.byref(h)), "gse_encode_table")
+        if num_exp:      # the paper's global exponent table (Sec. III-B)
+            samp = None
+            if sample_block_rows:        # sampled extraction: one row per block, drawn by the caller
+                samp = np.ascontiguousarray(sample_rows, dtype=np.int64)
+                if samp.size != (n_rows + sample_block_rows - 1) // sample_block_rows:
+                    raise ValueError("sample_rows needs one row index per block of sample_block_rows rows")
+            _check(L.gse_encode_table_ex(ctypes.byref(self.csr), num_exp, ctypes.cast(sb, _P), len(seg_bits),
+                                         index_place, int(sample_block_rows),
+                                         None if samp is None else samp.ctypes.data, self.stream, ctypes.byref(h)),
+                   "gse_encode_table_ex")
         else:
             _check(L.gse_encode(ctypes.byref(self.csr), group_size, ctypes.cast(sb, _P), len(seg_bits),
                                 self.stream, ctypes.byref(h)), "gse_encode")

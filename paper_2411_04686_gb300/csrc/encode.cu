@@ -99,12 +99,43 @@ __global__ void k_exp_hist(const double* __restrict__ val, int64_t nnz, unsigned
         if (h[i]) atomicAdd(hist + i, (unsigned long long)h[i]);
 }
 
+// Largest biased exponent among the finite values (the sampled extraction
+// still needs max + 1 of the whole matrix; Inf/NaN are flagged by the encoder).
+__global__ void k_exp_max(const double* __restrict__ val, int64_t nnz, int* emax) {
+    int m = 0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
+        const int ex = (int)(((uint64_t)__double_as_longlong(val[e]) >> 52) & 0x7FFu);
+        if (ex != 0x7FF) m = max(m, ex);
+    }
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(emax, m);
+}
+
+// Sampled extraction (Sec. III-B): one warp per row block b reads the block's
+// sampled row and counts each of its exponents once per row of the block.
+__global__ void k_exp_hist_sampled(const int32_t* __restrict__ row_ptr, const double* __restrict__ val, int64_t n_rows,
+                                   int64_t block_rows, const int64_t* __restrict__ sample, int64_t n_blocks,
+                                   unsigned long long* hist) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < n_blocks; b += warps) {
+        const int64_t first = b * block_rows;
+        const unsigned long long w = (unsigned long long)(first + block_rows <= n_rows ? block_rows : n_rows - first);
+        const int64_t r = sample[b];
+        for (int64_t j = row_ptr[r] + lane; j < row_ptr[r + 1]; j += 32) {
+            const int ex = (int)(((uint64_t)__double_as_longlong(val[j]) >> 52) & 0x7FFu);
+            if (ex != 0 && ex != 0x7FF) atomicAdd(hist + ex, w);
+        }
+    }
+}
+
 // Alg. 1 against the table through a per-exponent lookup: lut[e] = index | d << 8
 // (the entry equal to e + 1 with d = 1, else the nearest larger entry T with
 // d = T - e), then the segment split of k_encode.  The index is stored in the
-// top bits of the column word.
+// top bits of the column word (ei_shift < 32), or, with hb > 0, in the hb head
+// bits right below the sign; p then carries the widths shortened by hb.
 __global__ void k_encode_table(const double* __restrict__ val, const int32_t* __restrict__ col_in, int64_t nnz,
-                               int64_t nnz_pad, EncParams p, const uint32_t* __restrict__ lut, int ei_shift,
+                               int64_t nnz_pad, EncParams p, const uint32_t* __restrict__ lut, int ei_shift, int hb,
                                int32_t* col, uint16_t* head, uint16_t* tail1, uint16_t* t2hi, uint32_t* t2lo,
                                int* err) {
     const unsigned FULL = 0xFFFFFFFFu;
@@ -127,7 +158,8 @@ __global__ void k_encode_table(const double* __restrict__ val, const int32_t* __
             M = sh >= 0 ? (S << sh) : (-sh < 64 ? (S >> (-sh)) : 0ull);
         }
         const uint32_t sign = (uint32_t)(b >> 63);
-        head[e] = (uint16_t)((sign << (p.s1 - 1)) | (uint32_t)(M >> (p.W - p.W1)));
+        const uint32_t hidx = hb > 0 ? idx << (p.s1 - 1 - hb) : 0u;
+        head[e] = (uint16_t)((sign << (p.s1 - 1)) | hidx | (uint32_t)(M >> (p.W - p.W1)));
         if (p.n_seg >= 2) tail1[e] = (uint16_t)((M >> (p.W - p.W2)) & ((1ull << p.s2) - 1));
         if (p.n_seg >= 3) {
             const uint32_t t2 = (uint32_t)(M & ((1ull << p.s3) - 1));
@@ -150,8 +182,10 @@ __global__ void k_encode_table(const double* __restrict__ val, const int32_t* __
 // Host side of the table: the num_exp most frequent exponents (count
 // descending, then exponent descending), each + 1, with max + 1 forced in
 // place of the last kept entry when it did not make the cut; then the lookup
-// of every exponent's entry and distance.  Returns the number of entries.
-static int build_table(const unsigned long long* hist, int num_exp, int16_t* table, uint32_t* lut) {
+// of every exponent's entry and distance.  emax_all >= 0 gives the largest
+// exponent when the histogram is a sample that may miss it.  Returns the number
+// of entries.
+static int build_table(const unsigned long long* hist, int emax_all, int num_exp, int16_t* table, uint32_t* lut) {
     int order[2047];
     int n_distinct = 0, emax = 0;
     for (int e = 2046; e >= 1; e--)
@@ -159,10 +193,13 @@ static int build_table(const unsigned long long* hist, int num_exp, int16_t* tab
             order[n_distinct++] = e;
             if (e > emax) emax = e;
         }
+    if (emax_all >= 0) emax = emax_all;
     std::stable_sort(order, order + n_distinct, [&](int a, int b) { return hist[a] > hist[b]; });
     int n = 0;
-    if (n_distinct == 0) {
+    if (emax == 0) {
         table[n++] = 0;
+    } else if (n_distinct == 0) {
+        table[n++] = (int16_t)(emax + 1);         // an empty sample: max + 1 alone
     } else {
         bool has_max = false;
         for (int i = 0; i < n_distinct && n < num_exp; i++) {
@@ -406,8 +443,17 @@ static int dev_alloc(T** p, size_t count, size_t* acc) {
     return GSE_OK;
 }
 
+// Options of the table format (num_exp 0: the per-group format).
+struct TableOpts {
+    int num_exp = 0;
+    int index_place = GSE_INDEX_AUTO;
+    int64_t block_rows = 0;             // > 0: sampled extraction, one row per block
+    const int64_t* sample_rows = nullptr;
+};
+
 static int encode_impl(const gse_csr* csr, int G, const int* seg_bits, int n_seg, cudaStream_t s,
-                       gse_matrix* h, int num_exp = 0) {
+                       gse_matrix* h, const TableOpts& topt) {
+    const int num_exp = topt.num_exp;
     const int64_t n = csr->n_rows, nnz = csr->nnz;
     h->group_size = G;
     h->n_seg = n_seg;
@@ -504,40 +550,77 @@ static int encode_impl(const gse_csr* csr, int G, const int* seg_bits, int n_seg
             v.tbl = 0;
             v.ei_shift = 32;
             v.col_mask = 0xFFFFFFFFu;
+            v.hi_shift = 0;
+            v.hi_mask = 0;
             h->num_exp = 0;
+            h->index_in_head = 0;
             if (num_exp > 0) {
                 // the table format: histogram on the device, table and lookup on the host
                 unsigned long long* d_hist = nullptr;
                 uint32_t* d_lut = nullptr;
-                if (dev_alloc(&d_hist, 2048, &tacc) != GSE_OK || dev_alloc(&d_lut, 2048, &tacc) != GSE_OK) {
+                int64_t* d_sample = nullptr;
+                const bool sampled = topt.block_rows > 0;
+                const int64_t n_blocks = sampled ? (n + topt.block_rows - 1) / topt.block_rows : 0;
+                if (dev_alloc(&d_hist, 2048, &tacc) != GSE_OK || dev_alloc(&d_lut, 2048, &tacc) != GSE_OK ||
+                    (sampled && dev_alloc(&d_sample, (size_t)n_blocks + 1, &tacc) != GSE_OK)) {
                     status = GSE_ERR_OOM;
                 } else {
                     cudaMemsetAsync(d_hist, 0, 2048 * sizeof(unsigned long long), s);
-                    if (nnz > 0) k_exp_hist<<<h->num_sms * 4, 512, 0, s>>>(val, nnz, d_hist);
+                    int emax_all = -1;
+                    if (sampled) {
+                        // the largest exponent over all values, then the sampled rows' counts
+                        cudaMemsetAsync(d_err + 7, 0, sizeof(int), s);
+                        if (nnz > 0) k_exp_max<<<h->num_sms * 4, 512, 0, s>>>(val, nnz, d_err + 7);
+                        cudaMemcpyAsync(d_sample, topt.sample_rows, n_blocks * sizeof(int64_t), cudaMemcpyHostToDevice, s);
+                        if (n_blocks > 0)
+                            k_exp_hist_sampled<<<grid_for(n_blocks * 32), 256, 0, s>>>(rp, val, n, topt.block_rows,
+                                                                                      d_sample, n_blocks, d_hist);
+                        cudaMemcpyAsync(&emax_all, d_err + 7, sizeof(int), cudaMemcpyDeviceToHost, s);
+                    } else if (nnz > 0) {
+                        k_exp_hist<<<h->num_sms * 4, 512, 0, s>>>(val, nnz, d_hist);
+                    }
                     std::vector<unsigned long long> hist(2048);
                     cudaMemcpyAsync(hist.data(), d_hist, 2048 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
                     if (cudaStreamSynchronize(s) != cudaSuccess) status = GSE_ERR_CUDA;
                     std::vector<uint32_t> lut(2048);
                     int16_t table[64] = {0};
-                    const int nt = status == GSE_OK ? build_table(hist.data(), num_exp, table, lut.data()) : 1;
+                    const int nt = status == GSE_OK ? build_table(hist.data(), emax_all, num_exp, table, lut.data()) : 1;
                     int ei_bits = 0;
                     while ((1 << ei_bits) < nt) ei_bits++;
-                    if (status == GSE_OK && ei_bits > 0 && v.n_cols > (int64_t)(0xFFFFFFFFu >> ei_bits) + 1)
-                        status = GSE_ERR_UNSUPPORTED;     // the column index needs the bits the exponent index takes
+                    // where the index goes: the column word while its spare bits hold it
+                    // (Sec. III-C), else the head right below the sign
+                    const bool col_fits = ei_bits == 0 || v.n_cols <= (int64_t)(0xFFFFFFFFu >> ei_bits) + 1;
+                    const bool in_head = ei_bits > 0 && (topt.index_place == GSE_INDEX_VALUE ||
+                                                         (topt.index_place == GSE_INDEX_AUTO && !col_fits));
+                    if (status == GSE_OK && !in_head && !col_fits) status = GSE_ERR_UNSUPPORTED;
+                    if (status == GSE_OK && in_head && ei_bits > v.s1 - 2) status = GSE_ERR_UNSUPPORTED;
+                    const int hb = in_head ? ei_bits : 0;
+                    int16_t dtab[64] = {0};
+                    for (int i = 0; i < nt; i++) dtab[i] = (int16_t)(table[i] + hb);
                     int16_t* d_etab = nullptr;
                     if (status == GSE_OK && dev_alloc(&d_etab, 64, &h->bytes_matrix) != GSE_OK) status = GSE_ERR_OOM;
                     if (status == GSE_OK) {
                         h->buf_etab = d_etab;
-                        cudaMemcpyAsync(d_etab, table, sizeof(table), cudaMemcpyHostToDevice, s);
+                        cudaMemcpyAsync(d_etab, dtab, sizeof(dtab), cudaMemcpyHostToDevice, s);
                         v.etab = d_etab;
                         v.tbl = 1;
-                        v.ei_shift = 32 - ei_bits;
-                        v.col_mask = 0xFFFFFFFFu >> ei_bits;
+                        if (in_head) {
+                            v.hi_shift = v.s1 - 1 - hb;
+                            v.hi_mask = (1u << hb) - 1u;
+                        } else {
+                            v.ei_shift = 32 - ei_bits;
+                            v.col_mask = 0xFFFFFFFFu >> ei_bits;
+                        }
                         memcpy(h->etab_host, table, sizeof(table));
                         h->num_exp = nt;
+                        h->index_in_head = in_head;
+                        EncParams pt = p;        // widths shortened by the index bits in the head
+                        pt.W -= hb;
+                        pt.W1 -= hb;
+                        pt.W2 -= hb;
                         cudaMemcpyAsync(d_lut, lut.data(), 2048 * sizeof(uint32_t), cudaMemcpyHostToDevice, s);
                         cudaMemsetAsync(h->buf_gexp, 0, npad / G * sizeof(uint16_t), s);
-                        k_encode_table<<<grid_for(npad), 256, 0, s>>>(val, d_colin, nnz, npad, p, d_lut, v.ei_shift,
+                        k_encode_table<<<grid_for(npad), 256, 0, s>>>(val, d_colin, nnz, npad, pt, d_lut, v.ei_shift, hb,
                                                                       (int32_t*)h->buf_col, (uint16_t*)h->buf_head,
                                                                       (uint16_t*)h->buf_tail1, (uint16_t*)h->buf_t2hi,
                                                                       (uint32_t*)h->buf_t2lo, d_err);
@@ -546,6 +629,7 @@ static int encode_impl(const gse_csr* csr, int G, const int* seg_bits, int n_seg
                 }
                 if (d_hist) cudaFree(d_hist);
                 if (d_lut) cudaFree(d_lut);
+                if (d_sample) cudaFree(d_sample);
             } else {
                 k_encode<<<grid_for(npad), 256, 0, s>>>(val, d_colin, nnz, npad, p, (int32_t*)h->buf_col,
                                                         (uint16_t*)h->buf_head, (uint16_t*)h->buf_tail1,
@@ -627,7 +711,7 @@ static int encode_impl(const gse_csr* csr, int G, const int* seg_bits, int n_seg
 }
 
 static int encode_entry(const gse_csr* csr, int group_size, const int* seg_bits, int n_seg, void* stream,
-                        gse_handle* out, int num_exp) {
+                        gse_handle* out, const TableOpts& topt) {
     if (!csr || !seg_bits || !out) return GSE_ERR_INVALID;
     *out = nullptr;
     if (csr->n_rows < 0 || csr->n_cols < 0 || csr->nnz < 0 || csr->nnz >= (1LL << 31) ||
@@ -643,12 +727,21 @@ static int encode_entry(const gse_csr* csr, int group_size, const int* seg_bits,
         if (s3 > 16 && s3 != 20 && s3 != 24 && s3 != 32) return GSE_ERR_UNSUPPORTED;
     }
     if (group_size != 8 && group_size != 16 && group_size != 32) return GSE_ERR_UNSUPPORTED;
+    if (topt.block_rows > 0) {
+        // one sampled row per block of block_rows rows, inside its block (host array)
+        if (!topt.sample_rows && csr->n_rows > 0) return GSE_ERR_INVALID;
+        const int64_t nb = (csr->n_rows + topt.block_rows - 1) / topt.block_rows;
+        for (int64_t b = 0; b < nb; b++) {
+            const int64_t r = topt.sample_rows[b], lo = b * topt.block_rows;
+            if (r < lo || r >= lo + topt.block_rows || r >= csr->n_rows) return GSE_ERR_INVALID;
+        }
+    }
     gse_matrix* h = (gse_matrix*)calloc(1, sizeof(gse_matrix));
     if (!h) return GSE_ERR_OOM;
     cudaGetDevice(&h->device);
     cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
     if (h->num_sms < 1) h->num_sms = 1;
-    const int rc = encode_impl(csr, group_size, seg_bits, n_seg, (cudaStream_t)stream, h, num_exp);
+    const int rc = encode_impl(csr, group_size, seg_bits, n_seg, (cudaStream_t)stream, h, topt);
     if (rc != GSE_OK) {
         free_all(h);
         free(h);
@@ -660,14 +753,27 @@ static int encode_entry(const gse_csr* csr, int group_size, const int* seg_bits,
 
 extern "C" int gse_encode(const gse_csr* csr, int group_size, const int* seg_bits, int n_seg,
                           void* stream, gse_handle* out) {
-    return encode_entry(csr, group_size, seg_bits, n_seg, stream, out, 0);
+    return encode_entry(csr, group_size, seg_bits, n_seg, stream, out, TableOpts());
+}
+
+extern "C" int gse_encode_table_ex(const gse_csr* csr, int num_exp, const int* seg_bits, int n_seg, int index_place,
+                                   int64_t block_rows, const int64_t* sample_rows, void* stream, gse_handle* out) {
+    if (out) *out = nullptr;
+    if (num_exp < 1 || num_exp > 64 || block_rows < 0) return GSE_ERR_INVALID;
+    if (index_place != GSE_INDEX_AUTO && index_place != GSE_INDEX_COL && index_place != GSE_INDEX_VALUE)
+        return GSE_ERR_INVALID;
+    TableOpts t;
+    t.num_exp = num_exp;
+    t.index_place = index_place;
+    t.block_rows = block_rows;
+    t.sample_rows = sample_rows;
+    // group_size only sizes the (unused) group-exponent array here
+    return encode_entry(csr, 32, seg_bits, n_seg, stream, out, t);
 }
 
 extern "C" int gse_encode_table(const gse_csr* csr, int num_exp, const int* seg_bits, int n_seg, void* stream,
                                 gse_handle* out) {
-    if (num_exp < 1 || num_exp > 64) return GSE_ERR_INVALID;
-    // group_size only sizes the (unused) group-exponent array here
-    return encode_entry(csr, 32, seg_bits, n_seg, stream, out, num_exp);
+    return gse_encode_table_ex(csr, num_exp, seg_bits, n_seg, GSE_INDEX_AUTO, 0, nullptr, stream, out);
 }
 
 extern "C" int gse_export_table(gse_handle h, int16_t* table, int* n_table, uint8_t* idx) {
@@ -677,10 +783,16 @@ extern "C" int gse_export_table(gse_handle h, int16_t* table, int* n_table, uint
     if (n_table) *n_table = h->num_exp;
     const int64_t nnz = h->v.nnz;
     if (idx && nnz) {
-        std::vector<uint32_t> c(nnz);
-        GSE_CUDA_TRY(cudaMemcpy(c.data(), h->buf_col, nnz * sizeof(uint32_t), cudaMemcpyDeviceToHost));
-        for (int64_t e = 0; e < nnz; e++)
-            idx[e] = h->v.ei_shift < 32 ? (uint8_t)(c[e] >> h->v.ei_shift) : 0;
+        if (h->index_in_head) {
+            std::vector<uint16_t> hd(nnz);
+            GSE_CUDA_TRY(cudaMemcpy(hd.data(), h->buf_head, nnz * sizeof(uint16_t), cudaMemcpyDeviceToHost));
+            for (int64_t e = 0; e < nnz; e++) idx[e] = (uint8_t)((hd[e] >> h->v.hi_shift) & h->v.hi_mask);
+        } else {
+            std::vector<uint32_t> c(nnz);
+            GSE_CUDA_TRY(cudaMemcpy(c.data(), h->buf_col, nnz * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+            for (int64_t e = 0; e < nnz; e++)
+                idx[e] = h->v.ei_shift < 32 ? (uint8_t)(c[e] >> h->v.ei_shift) : 0;
+        }
     }
     return GSE_OK;
 }
@@ -818,6 +930,7 @@ extern "C" int gse_matrix_get_info(gse_handle h, gse_matrix_info* info) {
     info->mean_row_len = h->mean_row_len;
     info->schedule = units_per_lane(h);
     info->num_exp = h->num_exp;
+    info->index_in_head = h->index_in_head;
     info->overflow16 = h->overflow16;
     // algorithmic bytes: col + live segments + group exponent per nonzero,
     // row_ptr, x read once, y written once

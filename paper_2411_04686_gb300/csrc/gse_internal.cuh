@@ -14,7 +14,8 @@
 // for the whole matrix (each a frequent exponent + 1, max + 1 among them); the
 // index of a nonzero's entry sits in the top ei_bits bits of its col word
 // (col = index << (32 - ei_bits) | column), so every kernel masks col with
-// col_mask (all ones in the group format) and reads E = etab[col >> ei_shift].
+// col_mask (all ones in the group format) and reads E = etab[col >> ei_shift];
+// with the index in the head instead, E = etab[head index bits] (tbl_index).
 //   rowend  u32[nnz_pad / 32]         bit e: nonzero e is the last of its row
 //   blk_row0 int32[nnz_pad / 256]     compact index (nonempty rows only) of the
 //                                     row holding nonzero 256*b
@@ -60,17 +61,24 @@ struct MatView {
     int g_shift;               // log2(group size)
     int s1, s2, s3, s3hi, r_lo; // segment widths; s3hi = min(s3,16), r_lo = s3 - s3hi
     int W1, W2, W3;
-    int tbl;                   // 1: global exponent table (etab, index in col); 0: per-group gexp
-    int ei_shift;              // 32 - ei_bits (table format); the index is col >> ei_shift
+    int tbl;                   // 1: global exponent table (etab); 0: per-group gexp
+    int ei_shift;              // index in the col word: col >> ei_shift (32 when it is not there)
     uint32_t col_mask;         // column = col & col_mask
-    const int16_t* etab;       // the shared exponents (table format; device, 64 entries)
+    int hi_shift;              // index in the head: (head >> hi_shift) & hi_mask (hi_mask 0 when not)
+    uint32_t hi_mask;
+    const int16_t* etab;       // the shared exponents (table format; device, 64 entries); with
+                               // the index in the head each entry is stored + its bit count, so
+                               // the head, read as a full-width head, decodes unchanged
 };
 
 // Column index of a stored col word (strips the exponent index of the table format).
 __device__ __forceinline__ int32_t col_of(const MatView& m, int32_t c) { return (int32_t)((uint32_t)c & m.col_mask); }
-// Exponent-table index of a stored col word (table format).
-__device__ __forceinline__ int etab_index(const MatView& m, int32_t c) {
-    return (int)((uint64_t)(uint32_t)c >> m.ei_shift);
+// Exponent-table index of a table-format nonzero, from its col word or its head;
+// the index bits are cleared from the head (h) on the way.
+__device__ __forceinline__ int tbl_index(const MatView& m, int32_t c, uint32_t& h) {
+    const uint32_t hidx = (h >> m.hi_shift) & m.hi_mask;
+    h &= ~(m.hi_mask << m.hi_shift);
+    return (int)((uint64_t)(uint32_t)c >> m.ei_shift) | (int)hidx;
 }
 
 struct Workspace;  // solver vectors, allocated on first solve (solver.cu)
@@ -90,6 +98,7 @@ struct gse_matrix {
     int row_span256;     // ... of any 256-row block (standalone SpMV: 8-warp CTAs)
     int num_exp;         // table format: entries of the exponent table (0: group format)
     int16_t etab_host[64]; // table format: host copy of the table
+    int index_in_head;   // table format: 1 when the index sits in the head, 0 in the col word
     void* buf_etab;      // table format: the table on the device (64 entries)
     int schedule_forced; // 0: automatic
     int num_sms;

@@ -218,8 +218,8 @@ __device__ __forceinline__ void load_unit(const MatView& m, int64_t u, int* col,
         }
 #pragma unroll
         for (int i = 0; i < 8; i++) {
-            const uint32_t h = u16_of(hw, i);
-            const int Eg = m.tbl ? (int)__ldg(m.etab + etab_index(m, col[i])) : Eg0;   // table format: per value
+            uint32_t h = u16_of(hw, i);
+            const int Eg = m.tbl ? (int)__ldg(m.etab + tbl_index(m, col[i], h)) : Eg0;   // table format: per value
             if constexpr (K == 1) {
                 a[i] = decode_l1_f(h, Eg, (uint32_t)(Eg - m.W1 - 127) << 20, m);
             } else if constexpr (K == 2) {

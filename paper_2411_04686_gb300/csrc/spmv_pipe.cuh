@@ -163,7 +163,7 @@ __device__ __forceinline__ void issue_rows(const MatView& m, const RowStage& L, 
 
 // Value of the stage's nonzero i (stage-local index; its group is
 // (i >> g_shift) + goff in the stage's exponent run; in the table format the
-// shared exponent is etab[index in the col word cw]).
+// shared exponent is etab[index in the col word cw or in the head]).
 template <int K, int R, bool TBL = false>
 __device__ __forceinline__ double row_value(const MatView& m, const RowStage& L, const unsigned char* stage, int i,
                                             int goff, int32_t cw = 0, const int16_t* etab = nullptr) {
@@ -174,10 +174,10 @@ __device__ __forceinline__ double row_value(const MatView& m, const RowStage& L,
     } else if constexpr (src16(K)) {
         return widen16<K>(reinterpret_cast<const uint16_t*>(stage + L.off_v)[i]);
     } else {
-        const int Eg = TBL ? (int)etab[etab_index(m, cw)]
-                           : (int)reinterpret_cast<const uint16_t*>(stage + L.off_gx)[(i >> m.g_shift) + goff];
         const uint16_t* hv = reinterpret_cast<const uint16_t*>(stage + L.off_v);
-        const uint32_t h = hv[i];
+        uint32_t h = hv[i];
+        const int Eg = TBL ? (int)etab[tbl_index(m, cw, h)]
+                           : (int)reinterpret_cast<const uint16_t*>(stage + L.off_gx)[(i >> m.g_shift) + goff];
         if constexpr (K == 1) return decode_l1_f(h, Eg, (uint32_t)(Eg - m.W1 - 127) << 20, m);
         const uint32_t t1 = hv[L.span + i];
         if constexpr (K == 2) return decode_l2(h, t1, Eg, m);
@@ -438,8 +438,8 @@ __device__ __forceinline__ void unit_values_blk(const MatView& m, const ChunkSta
         }
 #pragma unroll
         for (int i = 0; i < 8; i++) {
-            const uint32_t h = u16_of(hw, i);
-            const int Eg = TBL ? (int)etab[etab_index(m, cw[i])] : Eg0;
+            uint32_t h = u16_of(hw, i);
+            const int Eg = TBL ? (int)etab[tbl_index(m, cw[i], h)] : Eg0;
             if constexpr (K == 1) {
                 a[i] = decode_l1_f(h, Eg, (uint32_t)(Eg - m.W1 - 127) << 20, m);
             } else if constexpr (K == 2) {

@@ -184,6 +184,16 @@ def uniform_x(n: int, seed: int = 0) -> np.ndarray:
     return np.random.default_rng(seed).uniform(-1.0, 1.0, size=n)
 
 
+def sample_rows(n_rows: int, block_rows: int, seed: int = 0) -> np.ndarray:
+    """One uniformly drawn row index per block of block_rows consecutive rows
+    (the last block may be shorter): the random choice of the sampled exponent
+    extraction, drawn here so that every consumer sees the same rows."""
+    rng = np.random.default_rng(seed)
+    first = np.arange(0, n_rows, block_rows, dtype=np.int64)
+    size = np.minimum(block_rows, n_rows - first)
+    return first + rng.integers(0, size, dtype=np.int64)
+
+
 def rhs_ones(A: CSR) -> np.ndarray:
     """b = A * ones (row sums), accumulated left to right in FP64."""
     rows = np.repeat(np.arange(A.n_rows), np.diff(A.row_ptr))
