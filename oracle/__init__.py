@@ -22,6 +22,7 @@ _lib = None
 
 OK, MAXITER, BREAKDOWN, NONFINITE = 0, 1, 2, 3
 POLICY_NO_STAGNATION = 1
+POLICY_FLOOR = 2
 
 
 def build(force: bool = False) -> str:

@@ -549,6 +549,7 @@ typedef struct {
 
 /* Policy flag: evaluate only the convergence check, never Conditions 1-3. */
 #define ORC_POLICY_NO_STAGNATION 1
+#define ORC_POLICY_FLOOR 2          /* the perturbation-floor trigger (beyond the paper) */
 
 /*
  * Plain FP64 CG (Hestenes-Stiefel), the FP64 baseline of Sec. IV.  Stops when
@@ -792,8 +793,25 @@ static int check_due(int j, const orc_policy* p)
  *    A_kmax decides: below tol stops; otherwise the solver steps (or, at
  *    k_max, restarts from the true residual);
  *  - p.Ap <= 0 at k < k_max is treated as a step, at k_max as a breakdown.
+ * With ORC_POLICY_FLOOR (an addition beyond the paper, reported apart from it):
+ * A_k differs from A_kmax by a perturbation whose infinity norm is
+ *   eta_k = max_i sum_j |a_kmax,ij - a_k,ij|,
+ * so once the recurrence residual falls to eta_k ||x|| / ||b|| (x the current
+ * iterate, 2-norms) level k has nothing more to give and the solver steps,
+ * before the stagnation check of that iteration.
  * hist (optional, capacity hist_cap) receives every recurrence residual.
  */
+static double level_gap(int64_t n, const int32_t* row_ptr, const double* hi, const double* lo)
+{
+    double eta = 0.0;
+    for (int64_t i = 0; i < n; i++) {
+        double s = 0.0;
+        for (int32_t e = row_ptr[i]; e < row_ptr[i + 1]; e++) s += fabs(hi[e] - lo[e]);
+        if (s > eta) eta = s;
+    }
+    return eta;
+}
+
 int orc_stepped_cg(int64_t n, const int32_t* row_ptr, const int32_t* col,
                    const double* const* a_levels, const double* b, double* x, double tol,
                    const orc_policy* pol, orc_info* info, double* hist, int hist_cap)
@@ -807,6 +825,9 @@ int orc_stepped_cg(int64_t n, const int32_t* row_ptr, const int32_t* col,
     int sw[3] = {-1, -1, -1};
     sw[k - 1] = 0;
     double nb = nrm2(n, b), res = 0.0, rho;
+    double eta[4] = {0.0, 0.0, 0.0, 0.0};
+    if (pol->flags & ORC_POLICY_FLOOR)
+        for (int kk = 1; kk < kmax; kk++) eta[kk] = level_gap(n, row_ptr, a_levels[kmax - 1], a_levels[kk - 1]);
     if (nb == 0.0) {
         for (int64_t i = 0; i < n; i++) x[i] = 0.0;
         status = ORC_OK;
@@ -841,6 +862,8 @@ int orc_stepped_cg(int64_t n, const int32_t* row_ptr, const int32_t* col,
                 if (tr < tol) { status = ORC_OK; break; }
                 if (k < kmax) { k++; sw[k - 1] = j; }
                 restart = 1;
+            } else if (k < kmax && (pol->flags & ORC_POLICY_FLOOR) && res <= eta[k] * nrm2(n, x) / nb) {
+                k++; sw[k - 1] = j; restart = 1;
             } else if (k < kmax && !(pol->flags & ORC_POLICY_NO_STAGNATION) &&
                        check_due(j, pol) && wlen >= pol->t + 1) {
                 double rsd, reldec; int ndec;

@@ -70,6 +70,25 @@ def test_floor_policy_steps_earlier_and_converges():
     assert np.max(np.abs(x - ref["x"])) < 1e-7
 
 
+@pytest.mark.parametrize("scale", [1.0, 1.0 / 30.0])
+def test_floor_policy_against_oracle(scale):
+    """The floor trigger on the GPU steps where the oracle's does: the GPU
+    reads ||x|| one iterate late (its x update runs after the decision), so the
+    switch iterations may differ by one or two."""
+    A = synth.laplace3d(16, shift=1e-3).scaled(scale)
+    for flags in (gse.POLICY_FLOOR, gse.POLICY_FLOOR | gse.POLICY_NO_STAGNATION):
+        pol = gse.Policy(**{**gse.SCALED_CG.__dict__, "flags": flags})
+        M, b, x, info = _solve(A, policy=pol)
+        opol = oracle.Policy(**{**oracle.SCALED_CG.__dict__, "flags": flags})
+        ref = oracle.stepped_cg(A.row_ptr, A.col, oracle.levels(A.val), b, tol=1e-10, policy=opol)
+        assert info["status"] == gse.OK and ref["info"]["status"] == oracle.OK
+        assert info["k_final"] == ref["info"]["k_final"] == 3
+        for i in (1, 2):
+            assert abs(info["switch_iter"][i] - ref["info"]["switch_iter"][i]) <= 3, (flags, info, ref["info"])
+        assert abs(info["iters"] - ref["info"]["iters"]) <= 4
+        assert np.max(np.abs(x - ref["x"])) < 1e-8 / scale
+
+
 def test_cg_zero_rhs_and_nonfinite():
     A = synth.poisson2d(8)
     M = gse.GseMatrix.from_csr(A)

@@ -151,3 +151,48 @@ def test_zero_rhs():
     for f in (oracle.stepped_cg, oracle.stepped_gmres):
         out = f(A.row_ptr, A.col, lv, b, x0=np.ones(A.n_rows), tol=1e-10, policy=oracle.SCALED_CG)
         assert out["info"]["status"] == oracle.OK and np.all(out["x"] == 0)
+
+
+def _floor_policy(flags):
+    return oracle.Policy(**{**oracle.SCALED_CG.__dict__, "flags": flags})
+
+
+def test_floor_trigger_fires_where_the_residual_meets_the_floor():
+    """The perturbation-floor trigger (beyond the paper): level k is left at the
+    first iteration j with ||r_j|| / ||b|| <= eta_k ||x_j|| / ||b||, eta_k the
+    infinity norm of A_3 - A_k.  Checked against the plain CG on A_1 (which
+    runs the stepped solver's level-1 arithmetic) and scipy's matrix norm."""
+    sp = pytest.importorskip("scipy.sparse")
+    # scaled so that no value is exact at level 1 (diagonal and off-diagonal
+    # errors have opposite signs) and ||x|| is about 30 ||b||
+    A = synth.laplace3d(10, shift=1e-3).scaled(1.0 / 30.0)
+    b = synth.rhs_ones(A)
+    lv = oracle.levels(A.val)
+    pol = _floor_policy(oracle.POLICY_FLOOR | oracle.POLICY_NO_STAGNATION)
+    out = oracle.stepped_cg(A.row_ptr, A.col, lv, b, tol=1e-10, policy=pol)
+    i = out["info"]
+    assert i["status"] == oracle.OK and i["k_final"] == 3 and i["rel_res_true"] < 1e-10
+    js = i["switch_iter"][1]
+    assert js > 0
+    eta = sp.linalg.norm(sp.csr_matrix((lv[2] - lv[0], A.col, A.row_ptr), shape=(A.n_rows, A.n_cols)), np.inf)
+    assert eta > 0
+    tr = oracle.cg(A.row_ptr, A.col, lv[0], b, tol=1e-30, max_iter=js, trace_n=js + 1)
+    nb = np.linalg.norm(b)
+    res = np.linalg.norm(tr["r"], axis=1) / nb
+    flo = eta * np.linalg.norm(tr["xs"], axis=1) / nb
+    assert np.linalg.norm(tr["xs"][js]) > 10 * nb
+    assert np.all(res[1:js] > flo[1:js])
+    assert res[js] <= flo[js]
+    # without the trigger (and without stagnation checks) level 1 runs on
+    no = oracle.stepped_cg(A.row_ptr, A.col, lv, b, tol=1e-10, policy=_floor_policy(oracle.POLICY_NO_STAGNATION))
+    assert no["info"]["switch_iter"][1] > js
+
+
+def test_floor_trigger_is_silent_when_the_head_is_exact():
+    # values 4 and -1 are exact at level 1: eta = 0, so the trigger never fires
+    A = synth.poisson2d(32)
+    b = synth.rhs_ones(A)
+    lv = oracle.levels(A.val)
+    a = oracle.stepped_cg(A.row_ptr, A.col, lv, b, tol=1e-10, policy=_floor_policy(oracle.POLICY_FLOOR))
+    c = oracle.stepped_cg(A.row_ptr, A.col, lv, b, tol=1e-10, policy=oracle.SCALED_CG)
+    assert a["info"] == c["info"] and np.array_equal(a["x"], c["x"])
