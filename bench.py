@@ -384,17 +384,18 @@ def main():
 
     # the paper's default format: one global table of numExp shared exponents
     # (Sec. III-B), the index in the column word (Sec. III-C); per-level times
-    # at numExp = 8 and the numExp sweep of Sec. IV-B (time and max |y - y_FP64|)
+    # at numExp = 8 and the numExp sweep of Sec. IV-B (time and max |y - y_FP64|);
+    # then numExp = 8 with the index kept in the head (Sec. III-C's layout for
+    # columns without spare bits) and with the sampled extraction (Sec. III-B,
+    # one row per 64-row block), with the encode's wall time beside the exact one
     table = None
     if not args.no_table:
         table = {}
         for name, A, M, x, y in handles:
             y64 = M.spmv(gse.LEVEL_FP64, x).clone()
-            sweep = {}
-            for ne in (2, 4, 8, 16, 32, 64):
-                T = gse.GseMatrix.from_csr(A, num_exp=ne)
-                row = {"entries": T.info().num_exp}
-                for k in ((1, 2, 3) if ne == 8 else (1,)):
+
+            def measure(T, levels, row):
+                for k in levels:
                     ts = []
                     for r in range(10):
                         flush_l2(r)
@@ -409,8 +410,40 @@ def main():
                     row[f"k{k}_us"] = round(ms * 1e3, 2)
                     row[f"k{k}_GB_s"] = round(nb / (ms * 1e-3) / 1e9, 1)
                     row[f"k{k}_max_abs_err_vs_fp64"] = float((T.spmv(k, x) - y64).abs().max().item())
-                sweep[f"num_exp_{ne}"] = row
+                return row
+
+            sweep = {}
+            for ne in (2, 4, 8, 16, 32, 64):
+                T = gse.GseMatrix.from_csr(A, num_exp=ne)
+                sweep[f"num_exp_{ne}"] = measure(T, (1, 2, 3) if ne == 8 else (1,), {"entries": T.info().num_exp})
                 T.free()
+            T = gse.GseMatrix.from_csr(A, num_exp=8, index_place=gse.INDEX_VALUE)
+            sweep["num_exp_8_index_in_head"] = measure(T, (1, 2, 3), {"entries": T.info().num_exp,
+                                                                      "index_in_head": T.info().index_in_head})
+            T.free()
+            # encode wall time from a device-resident CSR: exact vs sampled counts
+            dA = [torch.from_numpy(a).cuda() for a in (A.row_ptr, A.col, A.val)]
+            srows = synth.sample_rows(A.n_rows, 64, seed=0)
+            enc_ms = {}
+            for tag, kw in (("exact", {}), ("sampled_64", {"sample_block_rows": 64, "sample_rows": srows})):
+                ts = []
+                for r in range(4):
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    T = gse.GseMatrix(*dA, n_cols=A.n_cols, num_exp=8, **kw)
+                    torch.cuda.synchronize()
+                    ts.append((time.perf_counter() - t0) * 1e3)
+                    if r < 3:
+                        T.free()
+                enc_ms[tag] = round(statistics.median(ts[1:]), 2)
+            full_table = gse.GseMatrix(*dA, n_cols=A.n_cols, num_exp=8)
+            row = {"entries": T.info().num_exp, "block_rows": 64,
+                   "same_table_as_exact": T.export_table()[0].tolist() == full_table.export_table()[0].tolist(),
+                   "encode_ms": enc_ms["sampled_64"], "encode_ms_exact": enc_ms["exact"]}
+            full_table.free()
+            sweep["num_exp_8_sampled_64"] = measure(T, (1,), row)
+            T.free()
+            del dA
             table[name] = sweep
 
     # e2e: through the C ABI with host buffers, copies inside the timed region

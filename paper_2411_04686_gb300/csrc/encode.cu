@@ -475,7 +475,7 @@ static int encode_impl(const gse_csr* csr, int G, const int* seg_bits, int n_seg
     v.W1 = sb[0] - 1;
     v.W2 = v.W1 + v.s2;
     v.W3 = v.W2 + v.s3;
-    const int64_t npad = v.nnz_pad, nblk = npad / 256, ngroups = (nnz + G - 1) / G;
+    const int64_t npad = v.nnz_pad, nblk = npad / 256;
     size_t acc = 0;
     int rc;
 #define ALLOC(ptr, T, cnt) \
@@ -498,7 +498,7 @@ static int encode_impl(const gse_csr* csr, int G, const int* seg_bits, int n_seg
     ALLOC(h->d_err, int, 4);
     h->bytes_matrix = acc;
     // temporaries
-    int *d_err = nullptr, *d_tmp = nullptr, *d_flag = nullptr, *d_flag2 = nullptr, *d_pos = nullptr;
+    int *d_err = nullptr, *d_flag = nullptr, *d_flag2 = nullptr, *d_pos = nullptr;
     int *d_scan_tmp = nullptr, *d_total = nullptr;
     double* d_val = nullptr;
     const int32_t* d_colin = nullptr;
@@ -511,7 +511,6 @@ static int encode_impl(const gse_csr* csr, int G, const int* seg_bits, int n_seg
               dev_alloc(&d_scan_tmp, nflags / SCAN_TILE + 2, &tacc) == GSE_OK &&
               dev_alloc(&d_total, 4, &tacc) == GSE_OK;
     if (ok && !csr->on_device) ok = dev_alloc(&d_val, nnz, &tacc) == GSE_OK && dev_alloc(&d_colin_own, nnz, &tacc) == GSE_OK;
-    (void)d_tmp;
     int status = GSE_OK;
     if (!ok) status = GSE_ERR_OOM;
     if (status == GSE_OK) {

@@ -364,7 +364,6 @@ extern "C" int gse_gmres(gse_handle h, const double* b, double* x, double tol, c
     int nblk = h->num_sms * 4;
     const int64_t need = (n + 255) / 256;
     if (nblk > need) nblk = (int)(need < 1 ? 1 : need);
-    int rc = GSE_OK;
     if (cudaMalloc(&w.V, (size_t)(m + 1) * n * sizeof(double) + 16) != cudaSuccess ||
         cudaMalloc(&w.partial, (size_t)(GM_MAX_RESTART + 2) * nblk * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&w.counter, 4 * sizeof(unsigned)) != cudaSuccess ||
