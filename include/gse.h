@@ -204,6 +204,22 @@ int gse_engine_cancel(gse_engine e, int slot, gse_solve_info* info);
 void gse_engine_destroy(gse_engine e);
 
 /*
+ * gse_engine_run in two halves, so the host can work while the device solves.
+ * gse_engine_launch queues max_slots iteration slots (in CUDA-graph batches of
+ * `batch`) and one copy of every system's state on the engine's stream, and
+ * returns without waiting.  gse_engine_wait blocks until that launch has
+ * finished, updates the host view of the states and sets *n_running (may be
+ * NULL) to the active systems not yet done.  A launch runs all max_slots slots
+ * (gse_engine_run stops early once nothing runs).  Between the two calls the
+ * caller may do any other work, including encoding new matrices on other
+ * streams; every other engine call (submit, run, poll, cancel, destroy) first
+ * waits for a pending launch itself.  Errors: GSE_ERR_INVALID (NULL engine,
+ * max_slots < 0), GSE_ERR_CUDA.
+ */
+int gse_engine_launch(gse_engine e, int max_slots, int batch);
+int gse_engine_wait(gse_engine e, int* n_running);
+
+/*
  * gse_cg_noalloc: the stepped CG of gse_cg for callers that cannot allocate
  * device memory once their set-up is done (a real-time loop with a fixed
  * memory budget, code under an allocator that forbids new allocations, a

@@ -28,7 +28,8 @@ EXPORTS = ["gse_strerror", "gse_encode", "gse_attach_values", "gse_spmv", "gse_c
            "gse_batch_cg", "gse_engine_create", "gse_engine_submit", "gse_engine_run",
            "gse_engine_poll", "gse_engine_cancel", "gse_engine_destroy", "gse_export", "gse_decode",
            "gse_matrix_get_info", "gse_set_schedule", "gse_autotune", "gse_footprint",
-           "gse_solve_footprint", "gse_free", "gse_encode_table", "gse_encode_table_ex", "gse_export_table"]
+           "gse_solve_footprint", "gse_free", "gse_encode_table", "gse_encode_table_ex", "gse_export_table",
+           "gse_engine_launch", "gse_engine_wait"]
 
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -101,6 +102,8 @@ def lib():
     L.gse_engine_create.argtypes = [_I, _P, ctypes.POINTER(_P)]
     L.gse_engine_submit.argtypes = [_P, _P, _P, _P, _D, ctypes.POINTER(StepPolicy), ctypes.POINTER(_I)]
     L.gse_engine_run.argtypes = [_P, _I, _I, ctypes.POINTER(_I)]
+    L.gse_engine_launch.argtypes = [_P, _I, _I]
+    L.gse_engine_wait.argtypes = [_P, ctypes.POINTER(_I)]
     L.gse_engine_poll.argtypes = [_P, _P, _P, _I, ctypes.POINTER(_I)]
     L.gse_engine_cancel.argtypes = [_P, _I, ctypes.POINTER(SolveInfo)]
     L.gse_engine_destroy.argtypes = [_P]
@@ -350,6 +353,16 @@ class Engine:
     def run(self, max_slots: int, batch: int = 8) -> int:
         n = ctypes.c_int(0)
         _check(lib().gse_engine_run(self.e, max_slots, batch, ctypes.byref(n)), "gse_engine_run")
+        return n.value
+
+    def launch(self, max_slots: int, batch: int = 8):
+        """Queues max_slots iteration slots and returns at once (gse_engine_launch)."""
+        _check(lib().gse_engine_launch(self.e, max_slots, batch), "gse_engine_launch")
+
+    def wait(self) -> int:
+        """Waits for the last launch; returns the systems still running."""
+        n = ctypes.c_int(0)
+        _check(lib().gse_engine_wait(self.e, ctypes.byref(n)), "gse_engine_wait")
         return n.value
 
     def poll(self):

@@ -4,11 +4,13 @@
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include "pool.cuh"
 #include "spmv_core.cuh"
 
 namespace gse {
@@ -404,8 +406,35 @@ static void free_all(gse_matrix* h) {
                     h->buf_rowend, h->buf_blk_row0, h->buf_nzrow, h->buf_empty, h->buf_row_ptr,
                     h->buf_val64, h->buf_val32, h->buf_val16, h->buf_valbf, h->buf_carry, h->buf_part, h->buf_etab,
                     h->red_partial, h->red_counter, h->red_result, h->d_err};
-    for (void* b : bufs)
-        if (b) cudaFree(b);
+    for (void* b : bufs) pool_free(b);
+}
+
+}  // namespace gse
+
+namespace gse {
+
+cudaMemPool_t device_pool() {
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!pools[dev]) {
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t p = nullptr;
+        if (cudaMemPoolCreate(&p, &props) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        uint64_t keep = UINT64_MAX;                  // freed blocks stay cached for the next matrix
+        cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+        pools[dev] = p;
+    }
+    return pools[dev];
 }
 
 }  // namespace gse
@@ -430,17 +459,10 @@ extern "C" const char* gse_strerror(int status) {
     }
 }
 
+// A buffer the handle keeps (from the library's pool, ordered on stream s).
 template <typename T>
-static int dev_alloc(T** p, size_t count, size_t* acc) {
-    if (count == 0) count = 1;
-    const size_t bytes = count * sizeof(T);
-    if (cudaMalloc((void**)p, bytes) != cudaSuccess) {
-        cudaGetLastError();
-        *p = nullptr;
-        return GSE_ERR_OOM;
-    }
-    *acc += bytes;
-    return GSE_OK;
+static int dev_alloc(T** p, size_t count, size_t* acc, cudaStream_t s) {
+    return pool_alloc(p, count, acc, s);
 }
 
 // Options of the table format (num_exp 0: the per-group format).
@@ -450,6 +472,15 @@ struct TableOpts {
     int64_t block_rows = 0;             // > 0: sampled extraction, one row per block
     const int64_t* sample_rows = nullptr;
 };
+
+// Encoder temporaries come from the library's pool and go back with
+// cudaFreeAsync on the encoder's stream: allocating and releasing them never
+// waits for other streams' work (cudaFree would wait for the whole device, e.g.
+// a solver batch running while the next matrix encodes).
+template <typename T>
+static int tmp_alloc(T** p, size_t count, cudaStream_t s) {
+    return pool_alloc(p, count, nullptr, s);
+}
 
 static int encode_impl(const gse_csr* csr, int G, const int* seg_bits, int n_seg, cudaStream_t s,
                        gse_matrix* h, const TableOpts& topt) {
@@ -479,7 +510,7 @@ static int encode_impl(const gse_csr* csr, int G, const int* seg_bits, int n_seg
     size_t acc = 0;
     int rc;
 #define ALLOC(ptr, T, cnt) \
-    do { T* _p; if ((rc = dev_alloc(&_p, (size_t)(cnt), &acc)) != GSE_OK) return rc; ptr = _p; } while (0)
+    do { T* _p; if ((rc = dev_alloc(&_p, (size_t)(cnt), &acc, s)) != GSE_OK) return rc; ptr = _p; } while (0)
     ALLOC(h->buf_row_ptr, int32_t, n + 1);
     ALLOC(h->buf_col, int32_t, npad);
     ALLOC(h->buf_head, uint16_t, npad);
@@ -503,14 +534,13 @@ static int encode_impl(const gse_csr* csr, int G, const int* seg_bits, int n_seg
     double* d_val = nullptr;
     const int32_t* d_colin = nullptr;
     int32_t* d_colin_own = nullptr;
-    size_t tacc = 0;
     const int64_t nflags = n > nblk ? n : nblk;
-    if ((rc = dev_alloc(&d_err, 8, &tacc)) != GSE_OK) return rc;
-    bool ok = dev_alloc(&d_flag, nflags + 1, &tacc) == GSE_OK && dev_alloc(&d_flag2, nflags + 1, &tacc) == GSE_OK &&
-              dev_alloc(&d_pos, nflags + 1, &tacc) == GSE_OK &&
-              dev_alloc(&d_scan_tmp, nflags / SCAN_TILE + 2, &tacc) == GSE_OK &&
-              dev_alloc(&d_total, 4, &tacc) == GSE_OK;
-    if (ok && !csr->on_device) ok = dev_alloc(&d_val, nnz, &tacc) == GSE_OK && dev_alloc(&d_colin_own, nnz, &tacc) == GSE_OK;
+    if ((rc = tmp_alloc(&d_err, 8, s)) != GSE_OK) return rc;
+    bool ok = tmp_alloc(&d_flag, nflags + 1, s) == GSE_OK && tmp_alloc(&d_flag2, nflags + 1, s) == GSE_OK &&
+              tmp_alloc(&d_pos, nflags + 1, s) == GSE_OK &&
+              tmp_alloc(&d_scan_tmp, nflags / SCAN_TILE + 2, s) == GSE_OK &&
+              tmp_alloc(&d_total, 4, s) == GSE_OK;
+    if (ok && !csr->on_device) ok = tmp_alloc(&d_val, nnz, s) == GSE_OK && tmp_alloc(&d_colin_own, nnz, s) == GSE_OK;
     int status = GSE_OK;
     if (!ok) status = GSE_ERR_OOM;
     if (status == GSE_OK) {
@@ -560,8 +590,8 @@ static int encode_impl(const gse_csr* csr, int G, const int* seg_bits, int n_seg
                 int64_t* d_sample = nullptr;
                 const bool sampled = topt.block_rows > 0;
                 const int64_t n_blocks = sampled ? (n + topt.block_rows - 1) / topt.block_rows : 0;
-                if (dev_alloc(&d_hist, 2048, &tacc) != GSE_OK || dev_alloc(&d_lut, 2048, &tacc) != GSE_OK ||
-                    (sampled && dev_alloc(&d_sample, (size_t)n_blocks + 1, &tacc) != GSE_OK)) {
+                if (tmp_alloc(&d_hist, 2048, s) != GSE_OK || tmp_alloc(&d_lut, 2048, s) != GSE_OK ||
+                    (sampled && tmp_alloc(&d_sample, (size_t)n_blocks + 1, s) != GSE_OK)) {
                     status = GSE_ERR_OOM;
                 } else {
                     cudaMemsetAsync(d_hist, 0, 2048 * sizeof(unsigned long long), s);
@@ -597,7 +627,7 @@ static int encode_impl(const gse_csr* csr, int G, const int* seg_bits, int n_seg
                     int16_t dtab[64] = {0};
                     for (int i = 0; i < nt; i++) dtab[i] = (int16_t)(table[i] + hb);
                     int16_t* d_etab = nullptr;
-                    if (status == GSE_OK && dev_alloc(&d_etab, 64, &h->bytes_matrix) != GSE_OK) status = GSE_ERR_OOM;
+                    if (status == GSE_OK && dev_alloc(&d_etab, 64, &h->bytes_matrix, s) != GSE_OK) status = GSE_ERR_OOM;
                     if (status == GSE_OK) {
                         h->buf_etab = d_etab;
                         cudaMemcpyAsync(d_etab, dtab, sizeof(dtab), cudaMemcpyHostToDevice, s);
@@ -626,9 +656,9 @@ static int encode_impl(const gse_csr* csr, int G, const int* seg_bits, int n_seg
                         cudaStreamSynchronize(s);          // the lookup buffer is freed right below
                     }
                 }
-                if (d_hist) cudaFree(d_hist);
-                if (d_lut) cudaFree(d_lut);
-                if (d_sample) cudaFree(d_sample);
+                if (d_hist) cudaFreeAsync(d_hist, s);
+                if (d_lut) cudaFreeAsync(d_lut, s);
+                if (d_sample) cudaFreeAsync(d_sample, s);
             } else {
                 k_encode<<<grid_for(npad), 256, 0, s>>>(val, d_colin, nnz, npad, p, (int32_t*)h->buf_col,
                                                         (uint16_t*)h->buf_head, (uint16_t*)h->buf_tail1,
@@ -650,8 +680,8 @@ static int encode_impl(const gse_csr* csr, int G, const int* seg_bits, int n_seg
             v.n_empty = n - n_nonempty;
             if (status == GSE_OK && v.n_empty > 0) {
                 int32_t *nz, *em;
-                if (dev_alloc(&nz, (size_t)n_nonempty, &h->bytes_matrix) != GSE_OK ||
-                    (h->buf_nzrow = nz, dev_alloc(&em, (size_t)v.n_empty, &h->bytes_matrix)) != GSE_OK) {
+                if (dev_alloc(&nz, (size_t)n_nonempty, &h->bytes_matrix, s) != GSE_OK ||
+                    (h->buf_nzrow = nz, dev_alloc(&em, (size_t)v.n_empty, &h->bytes_matrix, s)) != GSE_OK) {
                     status = GSE_ERR_OOM;
                 } else {
                     h->buf_empty = em;
@@ -678,14 +708,14 @@ static int encode_impl(const gse_csr* csr, int G, const int* seg_bits, int n_seg
             }
         }
     }
-    cudaFree(d_err);
-    if (d_flag) cudaFree(d_flag);
-    if (d_flag2) cudaFree(d_flag2);
-    if (d_pos) cudaFree(d_pos);
-    if (d_scan_tmp) cudaFree(d_scan_tmp);
-    if (d_total) cudaFree(d_total);
-    if (d_val) cudaFree(d_val);
-    if (d_colin_own) cudaFree(d_colin_own);
+    cudaFreeAsync(d_err, s);
+    if (d_flag) cudaFreeAsync(d_flag, s);
+    if (d_flag2) cudaFreeAsync(d_flag2, s);
+    if (d_pos) cudaFreeAsync(d_pos, s);
+    if (d_scan_tmp) cudaFreeAsync(d_scan_tmp, s);
+    if (d_total) cudaFreeAsync(d_total, s);
+    if (d_val) cudaFreeAsync(d_val, s);
+    if (d_colin_own) cudaFreeAsync(d_colin_own, s);
     if (status != GSE_OK) return status;
     v.col = (const int32_t*)h->buf_col;
     v.head = (const uint16_t*)h->buf_head;
@@ -742,6 +772,7 @@ static int encode_entry(const gse_csr* csr, int group_size, const int* seg_bits,
     if (h->num_sms < 1) h->num_sms = 1;
     const int rc = encode_impl(csr, group_size, seg_bits, n_seg, (cudaStream_t)stream, h, topt);
     if (rc != GSE_OK) {
+        cudaStreamSynchronize((cudaStream_t)stream);     // nothing queued may still use the buffers
         free_all(h);
         free(h);
         return rc;
@@ -804,7 +835,7 @@ extern "C" int gse_attach_values(gse_handle h, const gse_csr* csr, int bits, voi
     const double* val = csr->val;
     double* tmp = nullptr;
     if (!csr->on_device) {
-        if (cudaMalloc(&tmp, (size_t)(h->v.nnz + 1) * sizeof(double)) != cudaSuccess) return GSE_ERR_OOM;
+        if (tmp_alloc(&tmp, (size_t)h->v.nnz + 1, s) != GSE_OK) return GSE_ERR_OOM;
         cudaMemcpyAsync(tmp, csr->val, h->v.nnz * sizeof(double), cudaMemcpyHostToDevice, s);
         val = tmp;
     }
@@ -815,9 +846,9 @@ extern "C" int gse_attach_values(gse_handle h, const gse_csr* csr, int bits, voi
         void*& buf = bits == GSE_LEVEL_FP16 ? h->buf_val16 : h->buf_valbf;
         uint16_t* v16 = nullptr;
         unsigned long long* d_ov = nullptr;
-        if (!buf) rc = dev_alloc(&v16, (size_t)h->v.nnz_pad, &h->bytes_matrix);
+        if (!buf) rc = dev_alloc(&v16, (size_t)h->v.nnz_pad, &h->bytes_matrix, s);
         if (rc == GSE_OK && v16) buf = v16;
-        if (rc == GSE_OK && cudaMalloc(&d_ov, sizeof(unsigned long long)) != cudaSuccess) rc = GSE_ERR_OOM;
+        if (rc == GSE_OK && tmp_alloc(&d_ov, 1, s) != GSE_OK) rc = GSE_ERR_OOM;
         if (rc == GSE_OK) {
             cudaMemsetAsync(d_ov, 0, sizeof(unsigned long long), s);
             k_round16<<<grid_for(h->v.nnz_pad), 256, 0, s>>>(val, h->v.nnz, h->v.nnz_pad, bits, (uint16_t*)buf, d_ov);
@@ -828,16 +859,13 @@ extern "C" int gse_attach_values(gse_handle h, const gse_csr* csr, int bits, voi
             if (bits == GSE_LEVEL_FP16) h->v.val16 = (const uint16_t*)buf;
             else h->v.valbf = (const uint16_t*)buf;
         }
-        if (d_ov) cudaFree(d_ov);
-        if (tmp) {
-            cudaStreamSynchronize(s);
-            cudaFree(tmp);
-        }
+        if (d_ov) cudaFreeAsync(d_ov, s);
+        if (tmp) cudaFreeAsync(tmp, s);
         if (rc == GSE_OK && cudaGetLastError() != cudaSuccess) rc = GSE_ERR_CUDA;
         return rc;
     }
-    if (bits == 64 && !h->buf_val64) rc = dev_alloc(&v64, (size_t)h->v.nnz_pad, &h->bytes_matrix);
-    if (bits == 32 && !h->buf_val32) rc = dev_alloc(&v32, (size_t)h->v.nnz_pad, &h->bytes_matrix);
+    if (bits == 64 && !h->buf_val64) rc = dev_alloc(&v64, (size_t)h->v.nnz_pad, &h->bytes_matrix, s);
+    if (bits == 32 && !h->buf_val32) rc = dev_alloc(&v32, (size_t)h->v.nnz_pad, &h->bytes_matrix, s);
     if (rc == GSE_OK) {
         if (v64) h->buf_val64 = v64;
         if (v32) h->buf_val32 = v32;
@@ -847,10 +875,7 @@ extern "C" int gse_attach_values(gse_handle h, const gse_csr* csr, int bits, voi
         h->v.val64 = (const double*)h->buf_val64;
         h->v.val32 = (const float*)h->buf_val32;
     }
-    if (tmp) {
-        cudaStreamSynchronize(s);
-        cudaFree(tmp);
-    }
+    if (tmp) cudaFreeAsync(tmp, s);
     if (cudaGetLastError() != cudaSuccess) return GSE_ERR_CUDA;
     return rc;
 }
@@ -950,8 +975,12 @@ extern "C" size_t gse_footprint(gse_handle h) {
 
 extern "C" void gse_free(gse_handle h) {
     if (!h) return;
-    cudaDeviceSynchronize();
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != h->device) cudaSetDevice(h->device);
+    cudaDeviceSynchronize();           // no queued work may still use the buffers
     gse_free_workspace(h);
     free_all(h);
+    if (cur != h->device) cudaSetDevice(cur);
     free(h);
 }

@@ -25,6 +25,7 @@
 #include <type_traits>
 #include <vector>
 
+#include "pool.cuh"
 #include "solver_internal.cuh"
 
 namespace gse {
@@ -519,8 +520,7 @@ void gse_free_workspace(gse_matrix* h) {
     if (!h->ws) return;
     Workspace* w = h->ws;
     void* bufs[] = {w->r, w->p, w->q, w->ring, w->partial, w->counter, w->V, w->gm_scratch};
-    for (void* b : bufs)
-        if (b) cudaFree(b);
+    for (void* b : bufs) pool_free(b);
     delete w;
     h->ws = nullptr;
     h->bytes_ws = 0;
@@ -531,26 +531,22 @@ static int ensure_cg_workspace(gse_matrix* h, cudaStream_t s) {
     Workspace* w = h->ws;
     const int64_t n = h->v.n_rows;
     if (!w->r) {
-        const size_t bytes = (size_t)(n + 1) * sizeof(double);
-        if (cudaMalloc(&w->r, bytes) != cudaSuccess || cudaMalloc(&w->p, bytes) != cudaSuccess ||
-            cudaMalloc(&w->q, bytes) != cudaSuccess) {
-            cudaGetLastError();
+        size_t acc = 0;
+        if (pool_alloc(&w->r, (size_t)n + 1, &acc, s) != GSE_OK || pool_alloc(&w->p, (size_t)n + 1, &acc, s) != GSE_OK ||
+            pool_alloc(&w->q, (size_t)n + 1, &acc, s) != GSE_OK)
             return GSE_ERR_OOM;
-        }
-        h->bytes_ws += 3 * bytes;
+        h->bytes_ws += acc;
         w->n = n;
     }
     if (!w->ring) {
-        if (cudaMalloc(&w->ring, (RING_MAX + 1) * sizeof(double)) != cudaSuccess) return GSE_ERR_OOM;
-        h->bytes_ws += (RING_MAX + 1) * sizeof(double);
+        if (pool_alloc(&w->ring, RING_MAX + 1, &h->bytes_ws, s) != GSE_OK) return GSE_ERR_OOM;
     }
     if (!w->partial) {
         w->partial_cap = h->num_sms * 64;
-        if (cudaMalloc(&w->partial, (size_t)w->partial_cap * sizeof(double)) != cudaSuccess ||
-            cudaMalloc(&w->counter, 8 * sizeof(unsigned)) != cudaSuccess)
+        if (pool_alloc(&w->partial, (size_t)w->partial_cap, &h->bytes_ws, s) != GSE_OK ||
+            pool_alloc(&w->counter, 8, &h->bytes_ws, s) != GSE_OK)
             return GSE_ERR_OOM;
         cudaMemsetAsync(w->counter, 0, 8 * sizeof(unsigned), s);
-        h->bytes_ws += (size_t)w->partial_cap * sizeof(double) + 8 * sizeof(unsigned);
     }
     return GSE_OK;
 }
@@ -632,9 +628,21 @@ struct gse_cg_engine {
     std::vector<SysDesc> h_sys;
     bool dirty = true;
     bool fresh = false;
+    bool pending = false;           // a gse_engine_launch whose state copy is not yet waited for
     cudaEvent_t ev[2];
 };
 
+
+// Every engine call other than gse_engine_launch first settles a launch still
+// in flight (gse_engine_wait), so host and device views of the states agree.
+extern "C" int gse_engine_wait(gse_engine e, int* n_running);
+#define ENGINE_SETTLE(e)                                      \
+    do {                                                      \
+        if ((e)->pending) {                                   \
+            const int _rc = gse_engine_wait((e), nullptr);    \
+            if (_rc != GSE_OK) return _rc;                    \
+        }                                                     \
+    } while (0)
 
 // The engine's stream waits for the caller's stream (its b and x are ready) ...
 static void engine_enter(gse_cg_engine* e) {
@@ -705,6 +713,7 @@ extern "C" int gse_engine_submit(gse_engine e, gse_handle h, const double* b, do
                                  const gse_step_policy* pol, int* slot_out) {
     if (!e || !h || !b || !x || !pol || !(tol > 0)) return GSE_ERR_INVALID;
     if (!level_valid(h, pol->k_start) || !level_valid(h, pol->k_max)) return GSE_ERR_INVALID;
+    ENGINE_SETTLE(e);
     const bool base = pol->k_start > 3 || pol->k_max > 3;
     if (base && pol->k_start != pol->k_max) return GSE_ERR_INVALID;
     if (!base && pol->k_start > pol->k_max) return GSE_ERR_INVALID;
@@ -867,6 +876,7 @@ static bool any_running(gse_cg_engine* e) {
 // `batch`, double-buffered); returns early when every active system is done.
 extern "C" int gse_engine_run(gse_engine e, int max_slots, int batch, int* n_running) {
     if (!e || max_slots < 0) return GSE_ERR_INVALID;
+    ENGINE_SETTLE(e);
     if (batch < 1) batch = 8;
     engine_enter(e);
     if (e->dirty) {
@@ -914,6 +924,52 @@ extern "C" int gse_engine_run(gse_engine e, int max_slots, int batch, int* n_run
     return GSE_OK;
 }
 
+// The asynchronous form of gse_engine_run: the slots and one copy of every
+// system's state are queued on the engine's stream and the call returns; the
+// host is free (to encode the next requests) until gse_engine_wait.
+extern "C" int gse_engine_launch(gse_engine e, int max_slots, int batch) {
+    if (!e || max_slots < 0) return GSE_ERR_INVALID;
+    if (batch < 1) batch = 8;
+    ENGINE_SETTLE(e);
+    engine_enter(e);
+    if (e->dirty) {
+        const int rc = rebuild_maps(e);
+        if (rc != GSE_OK) return rc;
+    }
+    if (e->nblk_vec == 0) return GSE_OK;
+    if (e->fresh) {
+        k_cg_init<<<e->nblk_vec, 256, 0, e->stream>>>(e->d_sys, e->d_map_vec);
+        k_cg_p3<<<e->nblk_vec, 256, 0, e->stream>>>(e->d_sys, e->d_map_vec);  // zero x for b = 0
+        e->fresh = false;
+    }
+    for (int done_slots = 0; done_slots < max_slots;) {
+        const int nb = max_slots - done_slots < batch ? max_slots - done_slots : batch;
+        run_slots(e, nb, batch);
+        done_slots += nb;
+    }
+    cudaMemcpyAsync(e->h_stage[0], e->d_state, e->capacity * sizeof(CgState), cudaMemcpyDeviceToHost, e->stream);
+    cudaEventRecord(e->ev[0], e->stream);
+    e->pending = true;
+    return cudaGetLastError() == cudaSuccess ? GSE_OK : GSE_ERR_CUDA;
+}
+
+extern "C" int gse_engine_wait(gse_engine e, int* n_running) {
+    if (!e) return GSE_ERR_INVALID;
+    if (e->pending) {
+        e->pending = false;
+        if (cudaEventSynchronize(e->ev[0]) != cudaSuccess) return GSE_ERR_CUDA;
+        memcpy(e->h_state, e->h_stage[0], e->capacity * sizeof(CgState));
+        engine_leave(e);
+    }
+    if (n_running) {
+        int c = 0;
+        for (int i = 0; i < e->capacity; i++)
+            if (e->slots[i].active && e->h_state[i].mode != MODE_DONE) c++;
+        *n_running = c;
+    }
+    return GSE_OK;
+}
+
 static void fill_info(gse_cg_engine* e, int slot, gse_solve_info* info, double rel_true) {
     const CgState& s = e->h_state[slot];
     info->status = s.mode == MODE_DONE ? s.status : GSE_MAXITER;
@@ -951,6 +1007,7 @@ static double true_residual(gse_cg_engine* e, int slot) {
 // Reports finished systems (slots and infos, up to max_done) and frees their slots.
 extern "C" int gse_engine_poll(gse_engine e, int* done_slots, gse_solve_info* infos, int max_done, int* n_done) {
     if (!e) return GSE_ERR_INVALID;
+    ENGINE_SETTLE(e);
     engine_enter(e);
     int c = 0;
     for (int i = 0; i < e->capacity && c < max_done; i++) {
@@ -977,6 +1034,7 @@ extern "C" int gse_engine_poll(gse_engine e, int* done_slots, gse_solve_info* in
 // Cancels a slot (its system stays where it is; info reports MAXITER).
 extern "C" int gse_engine_cancel(gse_engine e, int slot, gse_solve_info* info) {
     if (!e || slot < 0 || slot >= e->capacity || !e->slots[slot].active) return GSE_ERR_INVALID;
+    ENGINE_SETTLE(e);
     engine_enter(e);
     cudaStreamSynchronize(e->stream);
     cudaMemcpy(&e->h_state[slot], e->d_state + slot, sizeof(CgState), cudaMemcpyDeviceToHost);

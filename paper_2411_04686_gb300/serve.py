@@ -11,6 +11,12 @@ while earlier ones are still on the GPU.  Each result is independent of what
 else runs (the engine's per-system partition and reduction order depend only
 on the system), which the tests check bit for bit.
 
+A step is pipelined: the engine's slots are launched without waiting
+(``gse_engine_launch``), the host encodes the requests admitted into the slots
+freed by the previous step while the device runs them, and only then waits
+(``gse_engine_wait``), collects finished systems and submits the new ones.
+Encoding thus overlaps the solves instead of alternating with them.
+
 The admission rule (``admit``) and the footprint estimate
 (``estimate_footprint``) are plain host functions, tested on the CPU with a fake
 clock and a fake memory budget.
@@ -104,31 +110,35 @@ class Server:
         self.queue: deque = deque()
         self.active = {}                # slot -> (request, admitted time, placed system)
         self.done: list[Completion] = []
+        self.inflight = False           # an engine launch not yet waited for
 
     def submit(self, req: Request):
         if not req.footprint:
             req.footprint = estimate_footprint(req.n_rows, req.nnz)
         self.queue.append(req)
 
-    def _start(self, req: Request):
-        A, b = self.build(req.payload)
-        sysm = self.place(A, b)              # (matrix handle, b, x) resident on the device
-        slot = self.engine.submit(sysm[0], sysm[1], sysm[2], self.tol, self.policy)
-        self.active[slot] = (req, self.clock(), sysm)
-        self.used += req.footprint
-
     def step(self) -> int:
-        """Admit what fits, advance the batch, collect finished solves.
-        Returns the number of systems still running."""
-        free_slots = self.capacity - len(self.active)
-        for req in admit(self.queue, free_slots, self.mem_budget - self.used):
-            self._start(req)
-        running = self.engine.run(self.slots_per_step, batch=self.slots_per_step) if self.active else 0
+        """Encode what fits while the device runs the previous launch, then
+        collect finished solves, submit the encoded ones and launch the next
+        slots.  Returns the number of systems still running."""
+        ready = []
+        for req in admit(self.queue, self.capacity - len(self.active), self.mem_budget - self.used):
+            A, b = self.build(req.payload)
+            ready.append((req, self.clock(), self.place(A, b)))   # (matrix handle, b, x) on the device
+            self.used += req.footprint
+        running = self.engine.wait() if self.inflight else 0
+        self.inflight = False
         for slot, info in self.engine.poll():
             req, t_adm, sysm = self.active.pop(slot)
             self.done.append(Completion(req.rid, req.arrival, t_adm, self.clock(), info))
             self.used -= req.footprint
             sysm[0].free()
+        for req, t_adm, sysm in ready:
+            slot = self.engine.submit(sysm[0], sysm[1], sysm[2], self.tol, self.policy)
+            self.active[slot] = (req, t_adm, sysm)
+        if self.active:
+            self.engine.launch(self.slots_per_step, batch=self.slots_per_step)
+            self.inflight = True
         return running
 
     def drain(self):

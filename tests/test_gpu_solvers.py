@@ -168,6 +168,42 @@ def test_engine_continuous_batching_matches_solo():
         assert torch.equal(xs[i], x1)
 
 
+def test_engine_launch_wait_overlaps_encoding_and_matches_solo():
+    """gse_engine_launch returns before the slots run; matrices encoded while a
+    launch is in flight join at the next step and every result equals its solo
+    solve bit for bit."""
+    As = _systems(10, 7)
+    bs = [_dev(synth.rhs_ones(A)) for A in As]
+    eng = gse.Engine(4)
+    xs, mats, slot_of, results = {}, {}, {}, {}
+    pending, ready = list(range(len(As))), []
+    launched = False
+    while pending or slot_of or ready:
+        # encode while the previous launch runs
+        while pending and len(slot_of) + len(ready) < 4:
+            i = pending.pop(0)
+            mats[i] = gse.GseMatrix.from_csr(As[i])
+            xs[i] = torch.zeros(As[i].n_rows, dtype=torch.float64, device="cuda")
+            ready.append(i)
+        if launched:
+            eng.wait()
+        for s, info in eng.poll():
+            results[slot_of.pop(s)] = info
+        for i in ready:
+            slot_of[eng.submit(mats[i], bs[i], xs[i])] = i
+        ready = []
+        launched = bool(slot_of)
+        if launched:
+            eng.launch(7, batch=4)
+    eng.close()
+    for i, A in enumerate(As):
+        x1 = torch.zeros(A.n_rows, dtype=torch.float64, device="cuda")
+        i1 = mats[i].cg(bs[i], x1)
+        assert results[i]["status"] == gse.OK
+        assert results[i]["iters"] == i1["iters"]
+        assert torch.equal(xs[i], x1)
+
+
 @pytest.mark.parametrize("sched", [1, gse.SCHEDULE_ROWS])
 def test_stepped_cg_on_each_engine_schedule(sched):
     """The engine's SpMV phase runs either schedule; both reach the same answer."""

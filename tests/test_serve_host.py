@@ -44,6 +44,12 @@ class FakeEngine:
             v[0] -= nslots
         return sum(1 for v in self.slots.values() if v[0] > 0)
 
+    def launch(self, nslots, batch=8):
+        self.run(nslots, batch)
+
+    def wait(self):
+        return sum(1 for v in self.slots.values() if v[0] > 0)
+
     def poll(self):
         out = [(s, {"status": 0, "rid": v[1]}) for s, v in self.slots.items() if v[0] <= 0]
         for s, _ in out:
@@ -83,9 +89,13 @@ def test_continuous_batching_with_fake_engine_and_clock():
         clock["t"] += 1.0
         srv.step()
         order = [c.rid for c in srv.done]
-    # two slots and a budget for two: 0 and 1 start; 1 leaves after one step, 2 joins
-    # while 0 is still running (continuous batching), and so on
-    assert order == [1, 2, 0, 3, 4]
+    # two slots and a budget for two: 0 and 1 start; 1 leaves after one launch and
+    # 2 joins while 0 is still running (continuous batching), and so on; a freed
+    # slot is refilled one launch later, the next request being encoded while the
+    # device runs that launch
+    assert order == [1, 0, 2, 3, 4]
+    c = {x.rid: x for x in srv.done}
+    assert c[2].admitted < c[0].finished
     assert all(m.freed for m in placed)
     assert srv.used == 0
     lat = serve.latency_stats(srv.done)
