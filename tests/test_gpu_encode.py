@@ -28,8 +28,19 @@ def _random_csr(n, m, mean, seed, empty_frac=0.0, lo=-12, hi=12):
     return synth.CSR(rp.astype(np.int32), col.astype(np.int32), val, m, "random")
 
 
+def _extreme_csr():
+    """Values over the whole normal range (E_g up to 2047) with DBL_MAX, the
+    smallest normal exponents, a subnormal and -0.0 among them."""
+    A = _random_csr(2000, 1500, 8.0, 5, lo=-1020, hi=1020)
+    A.val[3] = np.finfo(np.float64).max
+    A.val[4] = 2.0 ** -1022
+    A.val[5] = -2.0 ** -1021
+    return A
+
+
 CASES = [
     ("poisson32", lambda: synth.poisson2d(32)),
+    ("extreme", _extreme_csr),
     ("poisson32_third", lambda: synth.poisson2d(32, 1.0 / 3.0)),
     ("random_ragged", lambda: _random_csr(3001, 2500, 9.0, 1, empty_frac=0.1)),
     ("powerlaw", lambda: synth.powerlaw_random(20000, 16.0, 2048, seed=2)),

@@ -38,8 +38,23 @@ def _one_long_row():
     return synth.CSR(rp, cols, val, n_cols, "long_row")
 
 
+def _extreme_range():
+    """Magnitudes 2^U(-1022, 1015): groups from the smallest normal exponents up
+    to E_g near the top, products down in the subnormal range (no row sum can
+    overflow)."""
+    rng = np.random.default_rng(13)
+    n, m = 3000, 3000
+    lens = rng.integers(1, 24, n)
+    rp = np.zeros(n + 1, np.int64)
+    np.cumsum(lens, out=rp[1:])
+    col = np.concatenate([np.sort(rng.choice(m, L, replace=False)) for L in lens])
+    val = rng.choice([-1.0, 1.0], rp[-1]) * 2.0 ** rng.uniform(-1022, 1015, rp[-1])
+    return synth.CSR(rp.astype(np.int32), col.astype(np.int32), val, m, "extreme_range")
+
+
 MATS = {
     "poisson32": lambda: synth.poisson2d(32),
+    "extreme_range": _extreme_range,
     "poisson32_third": lambda: synth.poisson2d(32, 1.0 / 3.0),
     "laplace3d_24": lambda: synth.laplace3d(24, shift=1e-3),
     "powerlaw_50k": lambda: synth.powerlaw_random(50000, 16.0, 2048, seed=11),
@@ -80,8 +95,9 @@ def test_spmv_levels_against_oracle(name, upl):
         assert np.array_equal(y.view(np.uint64), y2.view(np.uint64))
     y64 = M.spmv(gse.LEVEL_FP64, xd).cpu().numpy()
     check_spmv_rows(y64, A, A.val, x)
-    y32 = M.spmv(gse.LEVEL_FP32, xd).cpu().numpy()
-    check_spmv_rows(y32, A, A.val.astype(np.float32).astype(np.float64), x)
+    if name != "extreme_range":          # FP32 cannot hold these values (inf / 0)
+        y32 = M.spmv(gse.LEVEL_FP32, xd).cpu().numpy()
+        check_spmv_rows(y32, A, A.val.astype(np.float32).astype(np.float64), x)
     M.free()
 
 

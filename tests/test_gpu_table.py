@@ -18,8 +18,21 @@ import paper_2411_04686_gb300 as gse  # noqa: E402
 
 SEG = (16, 16, 20)
 
+
+def _extreme_range():
+    rng = np.random.default_rng(14)
+    n, m = 2000, 2000
+    lens = rng.integers(1, 20, n)
+    rp = np.zeros(n + 1, np.int64)
+    np.cumsum(lens, out=rp[1:])
+    col = np.concatenate([np.sort(rng.choice(m, L, replace=False)) for L in lens])
+    val = rng.choice([-1.0, 1.0], rp[-1]) * 2.0 ** rng.uniform(-1022, 1015, rp[-1])
+    return synth.CSR(rp.astype(np.int32), col.astype(np.int32), val, m, "extreme_range")
+
+
 MATS = {
     "poisson32_third": lambda: synth.poisson2d(32, 1.0 / 3.0),
+    "extreme_range": _extreme_range,
     "laplace3d_24": lambda: synth.laplace3d(24, shift=1e-3),
     "powerlaw_50k": lambda: synth.powerlaw_random(50000, 16.0, 2048, seed=11),
     "tiny": lambda: synth.CSR(np.array([0, 1, 3], np.int32), np.array([1, 0, 1], np.int32),

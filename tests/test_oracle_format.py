@@ -170,6 +170,33 @@ def test_zero_and_subnormal_groups_and_partial_group():
         assert np.all(dec[:35] == 0.0) and np.all(dec[35:] == 1.0)
 
 
+def test_extreme_exponent_groups_closed_form():
+    """The top and bottom of the exponent range, worked by hand (G = 4, 16/16/32,
+    W = 15 / 31 / 63).  Group 0 holds DBL_MAX, so E_g = 2046 + 1 = 2047.  Group 1
+    holds the smallest normal exponents, E_g = 2 + 1 = 3."""
+    big = np.finfo(np.float64).max
+    vals = np.array([big, 1.0, -2.0 ** 1000, 0.0,
+                     2.0 ** -1022, 1.75 * 2.0 ** -1022, 5e-324, -2.0 ** -1021])
+    seg = (16, 16, 32)
+    enc = oracle.encode(vals, 4, seg)
+    assert enc[3].tolist() == [2047, 3]
+    lv = [oracle.decode(*enc, k, 4, seg) for k in (1, 2, 3)]
+    # DBL_MAX: d = 1, M = (2^53 - 1) << 10; level 1 keeps the top 15 bits,
+    # (2^15 - 1) * 2^(2047 - 1023 - 15) = 2^1024 - 2^1009; level 3 is exact (63 >= 53 + 1)
+    assert lv[0][0] == (2.0 ** 15 - 1) * 2.0 ** 1009
+    assert lv[2][0] == big
+    # 1.0 is 1024 binades below E_g: M = 0 at every level
+    assert all(l[1] == 0.0 for l in lv)
+    # -2^1000: d = 24, M = 2^52 >> 13 = 2^39; level 1 keeps M >> 48 = 0, level 2
+    # keeps M >> 32 = 2^7, i.e. 2^7 * 2^(2047 - 1023 - 31) = 2^1000
+    assert lv[0][2] == 0.0 and lv[1][2] == -2.0 ** 1000 and lv[2][2] == -2.0 ** 1000
+    # group 1: 2^-1022 (d = 2) and 1.75 * 2^-1022 (d = 2) fit in the head's 15 bits,
+    # -2^-1021 has d = 1; the subnormal input gives M = 0 (R4)
+    for l in lv:
+        assert l[4] == 2.0 ** -1022 and l[5] == 1.75 * 2.0 ** -1022 and l[6] == 0.0 and l[7] == -2.0 ** -1021
+    assert enc[0][4] == 1 << 13 and enc[0][5] == 14336 and enc[0][7] == 0x8000 | (1 << 14)
+
+
 def test_nonfinite_rejected():
     for bad in (np.inf, -np.inf, np.nan):
         with pytest.raises(ValueError):
