@@ -204,7 +204,7 @@ def main():
     ap.add_argument("--profile-gmres", type=int, nargs=2, metavar=("N", "ITERS"), default=None,
                     help="no timing: FP64 GMRES(30) for ITERS iterations on the N^2 convection-diffusion "
                          "operator and exit; the target for ncu captures of the GMRES kernels")
-    ap.add_argument("--serve-requests", type=int, default=1000)
+    ap.add_argument("--serve-requests", type=int, default=10000)
     ap.add_argument("--serve-rates", default="0.5,1,2",
                     help="arrival rates as fractions of the measured saturated batch throughput")
     args = ap.parse_args()
