@@ -3,21 +3,23 @@
 //
 // Every system carries a small state machine in device memory; one iteration
 // "slot" is three kernels that each process all active systems:
-//   P1  SpMV phase   ITER:    q = A_k p and p.q          (fused epilogue)
+//   P1  SpMV phase   ITER:    q = A_k p and p.q          (fused epilogue); the
+//                             last block: alpha = rho / p.q and the breakdown test
 //                    RESID_R: r = b - A_k x              (restart at level k)
 //                    RESID_T: q = b - A_kmax x           (true-residual check)
-//   P2  vector 1     ITER:    alpha = rho / p.q, r -= alpha q, rho' = r.r,
-//                             then (last block) the residual history, Eqs. 3-6,
-//                             Conditions 1-3, the convergence check and the
-//                             next mode
+//   P2  vector 1     ITER:    r -= alpha q, rho' = r.r, then (last block) the
+//                             residual history, Eqs. 3-6, Conditions 1-3, the
+//                             convergence check and the next mode
 //                    RESID_R: rho = r.r      RESID_T: ||q||, decide
 //   P3  vector 2     x += alpha p (the x update is folded here, one pass) and
 //                    p = r + beta p, or p = r / r = p = q after a restart
-// The host only enqueues slots and reads the state array once per batch, so a
-// single solve runs without a host round trip per iteration, and a batch of
-// systems shares each launch.  Each system's blocks, chunks and reduction
-// order depend on its own size only, so a system gives bit-identical results
-// alone and inside any batch.
+// The host only enqueues slots (batches of them replayed from a captured CUDA
+// graph) and reads the state array once per batch, so a single solve runs
+// without a host round trip per iteration, and a batch of systems shares each
+// launch.  gse_engine_launch / gse_engine_wait split a batch so the host can
+// work (encode the next requests) while it runs.  Each system's blocks, chunks
+// and reduction order depend on its own size only, so a system gives
+// bit-identical results alone and inside any batch.
 #include <chrono>
 #include <cmath>
 #include <cstdlib>

@@ -1,6 +1,7 @@
-// spmv.cu -- standalone GSE-SpMV (gse_spmv) and the plain FP64 / FP32 CSR
-// baselines through the same TMA-staged chunk loop; schedule choice and
-// autotuning.
+// spmv.cu -- standalone GSE-SpMV (gse_spmv) and the plain FP64 / FP32 / FP16 /
+// BF16 CSR baselines through the same loops: the row schedule (k_spmv_rows),
+// the direct-load nonzero split (k_spmv_direct) and the staged nonzero split
+// (k_spmv); schedule choice and autotuning.
 #include <cstdio>
 #include <mutex>
 

@@ -4,9 +4,10 @@
 //
 // Schedule: nonzero-split.  A chunk is CH = 256 * UPL consecutive nonzeros,
 // processed by one warp; lane l owns UPL consecutive units of 8 nonzeros.  Each
-// value is rebuilt in registers with integer operations only (leading one by
-// CLZ, exponent from the group exponent, mantissa by shifts; no int->double
-// conversion and no FP64 scaling) and accumulated with exactly one DFMA.  Rows
+// value is rebuilt in registers with integer operations only (leading one from
+// the FP32 image of its segment or by CLZ, exponent from the shared exponent,
+// mantissa by shifts; no int->double conversion and no FP64 scaling) and
+// accumulated with exactly one DFMA.  Rows
 // that end inside a lane are finished there; a row that crosses lanes is
 // stitched by a segmented warp scan of the lane carries (skipped when every lane
 // sees a row end, which holds whenever rows are at most 8 long); a row that
