@@ -127,9 +127,8 @@ __device__ __forceinline__ double warp_sum8(const double* a, int lane) {
 
 // h_j = v_j . w for j <= i and |w|^2 (CGS step; pass 1 is the DGKS correction),
 // 8 dot products per sweep over w.
-__global__ void __launch_bounds__(256) k_gm_dots(GmState* st, const double* __restrict__ V, int64_t n, int i,
+__global__ void __launch_bounds__(256, 4) k_gm_dots(GmState* st, const double* __restrict__ V, int64_t n, int i,
                                                   int pass, double* partial, unsigned* counter) {
-    __shared__ double red[32];
     __shared__ double bpart[GM_MAX_RESTART + 2];
     __shared__ double wsum[8][8];
     __shared__ bool last;
@@ -141,7 +140,24 @@ __global__ void __launch_bounds__(256) k_gm_dots(GmState* st, const double* __re
         double a[8];
 #pragma unroll
         for (int u = 0; u < 8; u++) a[u] = 0.0;
-        for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+        int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        // two elements per step, all their loads in flight together; each sum
+        // still takes its terms in order of t
+        for (; t + stride < n; t += 2 * stride) {
+            const double w0 = w[t], w1 = w[t + stride];
+            double v0[8], v1[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const int j = jb + u;
+                v0[u] = j <= i ? V[(size_t)j * n + t] : w0;
+                v1[u] = j <= i ? V[(size_t)j * n + t + stride] : w1;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; u++)
+                if (jb + u < nv) a[u] = fma(w1, v1[u], fma(w0, v0[u], a[u]));
+        }
+        for (; t < n; t += stride) {
             const double wt = w[t];
 #pragma unroll
             for (int u = 0; u < 8; u++) {
@@ -167,12 +183,17 @@ __global__ void __launch_bounds__(256) k_gm_dots(GmState* st, const double* __re
     __syncthreads();
     if (!last) return;
     __threadfence();
-    for (int j = 0; j < nv; j++) {
+    // the columns' totals in parallel: one warp per column sums a lane-strided
+    // slice of its per-block partials and reduces by shuffles (no block-wide
+    // barrier per column in this serial tail)
+    for (int j = warp; j < nv; j += (int)(blockDim.x >> 5)) {
         double a = 0.0;
-        for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) a += __ldcg(partial + (size_t)j * gridDim.x + b);
-        a = block_sum(a, red);
-        if (threadIdx.x == 0) bpart[j] = a;
+        for (unsigned b = lane; b < gridDim.x; b += 32) a += __ldcg(partial + (size_t)j * gridDim.x + b);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
+        if (lane == 0) bpart[j] = a;
     }
+    __syncthreads();
     if (threadIdx.x == 0) {
         *counter = 0;
         if (pass == 0) {
@@ -184,7 +205,7 @@ __global__ void __launch_bounds__(256) k_gm_dots(GmState* st, const double* __re
         }
     }
 }
-__global__ void __launch_bounds__(256) k_gm_axpy(GmState* st, double* __restrict__ V, int64_t n, int i, int pass,
+__global__ void __launch_bounds__(256, 4) k_gm_axpy(GmState* st, double* __restrict__ V, int64_t n, int i, int pass,
                                                   double* partial, unsigned* counter) {
     __shared__ double red[32];
     __shared__ double tot[1];
@@ -203,7 +224,24 @@ __global__ void __launch_bounds__(256) k_gm_axpy(GmState* st, double* __restrict
         double v[4];
 #pragma unroll
         for (int q = 0; q < 4; q++) v[q] = t0 + q * stride < n ? si * w[t0 + q * stride] : 0.0;
-        for (int j = 0; j <= i; j++) {
+        // two basis vectors' loads in flight per step (the FMA chain over j
+        // keeps its order)
+        int j = 0;
+        for (; j + 1 <= i; j += 2) {
+            const double* vj = V + (size_t)j * n;
+            const double* vk = vj + n;
+            double a[4], b[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const bool in = t0 + q * stride < n;
+                a[q] = in ? vj[t0 + q * stride] : 0.0;
+                b[q] = in ? vk[t0 + q * stride] : 0.0;
+            }
+            const double c = -coef[j], d = -coef[j + 1];
+#pragma unroll
+            for (int q = 0; q < 4; q++) v[q] = fma(d, b[q], fma(c, a[q], v[q]));
+        }
+        for (; j <= i; j++) {
             const double c = -coef[j];
             const double* vj = V + (size_t)j * n;
 #pragma unroll
