@@ -271,40 +271,56 @@ __global__ void __launch_bounds__(256, 4) k_gm_axpy(GmState* st, double* __restr
 // Column i: h_{i+1,i} = ||w||, previous rotations, a new rotation, g, the
 // residual estimate |g_{i+1}| / ||b||, the history ring, stop tests.
 __global__ void k_gm_givens(GmState* st, double* ring, int ring_cap, int i, int m, int max_iter) {
-    if (threadIdx.x != 0 || st->stop) return;
+    // the column, the previous rotations and the scalars are loaded by the
+    // whole warp at once into shared memory; one thread then runs the serial
+    // recurrence there instead of on a chain of dependent global loads
+    __shared__ double Rc[GM_MAX_RESTART + 2], cs[GM_MAX_RESTART], sn[GM_MAX_RESTART];
+    __shared__ int stop;
+    if (threadIdx.x == 0) stop = st->stop;
+    for (int r = threadIdx.x; r <= i; r += blockDim.x) Rc[r] = st->hcol[r];
+    for (int r = threadIdx.x; r < i; r += blockDim.x) {
+        cs[r] = st->cs[r];
+        sn[r] = st->sn[r];
+    }
+    __syncthreads();
+    if (threadIdx.x != 0 || stop) return;
+    const double hn = st->wn, gi = st->g[i], nb = st->nb, tol = st->tol;
+    const int j = st->j, hpos = st->hpos, hlen = st->hlen;
     const int ld = m + 1;
-    double* Rc = st->R + (size_t)i * ld;
-    for (int r = 0; r <= i; r++) Rc[r] = st->hcol[r];
-    const double hn = st->wn;
+    double* Rg = st->R + (size_t)i * ld;
     Rc[i + 1] = hn;
     st->scale[i + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
     for (int r = 0; r < i; r++) {
         const double a = Rc[r], b = Rc[r + 1];
-        Rc[r] = st->cs[r] * a + st->sn[r] * b;
-        Rc[r + 1] = -st->sn[r] * a + st->cs[r] * b;
+        Rc[r] = cs[r] * a + sn[r] * b;
+        Rc[r + 1] = -sn[r] * a + cs[r] * b;
     }
     const double den = hypot(Rc[i], Rc[i + 1]);
     if (!(den > 0.0) || !isfinite(den)) {
+        for (int r = 0; r <= i + 1; r++) Rg[r] = Rc[r];
         st->lucky = 2;  // singular: cannot extend the least-squares problem
         st->stop = 1;
         st->i_done = i;
         return;
     }
-    st->cs[i] = Rc[i] / den;
-    st->sn[i] = Rc[i + 1] / den;
+    const double c = Rc[i] / den, sv = Rc[i + 1] / den;
+    st->cs[i] = c;
+    st->sn[i] = sv;
     Rc[i] = den;
     Rc[i + 1] = 0.0;
-    st->g[i + 1] = -st->sn[i] * st->g[i];
-    st->g[i] = st->cs[i] * st->g[i];
-    st->j = st->j + 1;
-    const double res = fabs(st->g[i + 1]) / st->nb;
+    for (int r = 0; r <= i + 1; r++) Rg[r] = Rc[r];
+    const double g1 = -sv * gi;
+    st->g[i + 1] = g1;
+    st->g[i] = c * gi;
+    st->j = j + 1;
+    const double res = fabs(g1) / nb;
     st->res = res;
-    ring[st->hpos] = res;
-    st->hpos = (st->hpos + 1) % ring_cap;
-    if (st->hlen < ring_cap) st->hlen = st->hlen + 1;
+    ring[hpos] = res;
+    st->hpos = (hpos + 1) % ring_cap;
+    if (hlen < ring_cap) st->hlen = hlen + 1;
     st->i_done = i + 1;
     if (hn == 0.0) st->lucky = 1;
-    if (!(res >= st->tol) || hn == 0.0 || st->j >= max_iter || !isfinite(res)) st->stop = 1;
+    if (!(res >= tol) || hn == 0.0 || j + 1 >= max_iter || !isfinite(res)) st->stop = 1;
 }
 
 // y = R^{-1} g (back substitution, i_done columns).
