@@ -333,7 +333,12 @@ size_t gse_footprint(gse_handle h);
  * hold in total, encoded matrix included (admission control). */
 size_t gse_solve_footprint(gse_handle h, int method, int restart);
 
-/* Releases the handle and all its device memory (NULL is a no-op). */
+/* Releases the handle and all its device memory (NULL is a no-op).  Waits for
+ * the device to finish queued work first (the buffers may still be in use).
+ * Handle and workspace memory comes from a stream-ordered pool the library
+ * keeps per device: freed blocks stay cached there for later handles and are
+ * not returned to the driver before the process exits, so a server that
+ * encodes and frees one matrix per request never calls cudaMalloc/cudaFree. */
 void gse_free(gse_handle h);
 
 #ifdef __cplusplus
