@@ -718,7 +718,7 @@ def _served_run(gse, serve, pool, nreq, rate, rank, world):
             for i in range(nreq)]
     if world > 1:
         reqs = serve.shard(reqs, rank, world)
-    srv = serve.Server(lambda i: pool[i], capacity=64, slots_per_step=16)
+    srv = serve.Server(lambda i: pool[i], capacity=64, slots_per_step=16, backlog_slots_per_step=32)
     t0 = time.perf_counter()
     srv.clock = lambda: time.perf_counter() - t0
     k = 0

@@ -85,11 +85,15 @@ class Server:
     """
 
     def __init__(self, build, capacity: int = 64, mem_budget: int | None = None, tol: float = 1e-10,
-                 policy=None, slots_per_step: int = 16, clock=time.perf_counter, engine=None, place=None):
+                 policy=None, slots_per_step: int = 16, clock=time.perf_counter, engine=None, place=None,
+                 backlog_slots_per_step: int | None = None):
         self.build = build
         self.capacity = capacity
         self.tol = tol
         self.slots_per_step = slots_per_step
+        # longer steps while requests wait: fewer host round trips when the
+        # device is the bottleneck, short steps (low latency) when it is not
+        self.backlog_slots_per_step = backlog_slots_per_step or slots_per_step
         self.clock = clock
         if engine is None:                 # the real device engine
             import torch
@@ -137,7 +141,8 @@ class Server:
             slot = self.engine.submit(sysm[0], sysm[1], sysm[2], self.tol, self.policy)
             self.active[slot] = (req, t_adm, sysm)
         if self.active:
-            self.engine.launch(self.slots_per_step, batch=self.slots_per_step)
+            n = self.backlog_slots_per_step if self.queue else self.slots_per_step
+            self.engine.launch(n, batch=n)
             self.inflight = True
         return running
 

@@ -122,3 +122,24 @@ def test_poisson_arrivals_and_shard():
     items = list(range(11))
     parts = [serve.shard(items, r, 3) for r in range(3)]
     assert sorted(sum(parts, [])) == items and all(parts)
+
+
+def test_longer_steps_only_while_requests_wait():
+    eng = FakeEngine(1, {0: 10, 1: 10})
+    steps = []
+    orig = eng.launch
+
+    def launch(n, batch=8):
+        steps.append(n)
+        orig(n, batch)
+
+    eng.launch = launch
+    srv = serve.Server(build=lambda rid: (rid, None), capacity=1, mem_budget=100, slots_per_step=4,
+                       clock=lambda: 0.0, engine=eng, place=lambda A, b: (FakeMatrix(A), None, None),
+                       backlog_slots_per_step=8)
+    for rid in range(2):
+        srv.submit(serve.Request(rid, 0.0, 1, 1, payload=rid, footprint=10))
+    while srv.queue or srv.active:
+        srv.step()
+    assert steps[0] == 8 and steps[-1] == 4          # request 1 waits at first, not at the end
+    assert [c.rid for c in srv.done] == [0, 1]
