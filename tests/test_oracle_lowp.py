@@ -75,3 +75,20 @@ def test_overflow_count():
     assert ov == 2                               # infinities already in the input are not overflows
     _, ov = oracle.round16(v, oracle.BF16)
     assert ov == 0
+
+
+@pytest.mark.parametrize("kind", [oracle.FP16, oracle.BF16])
+def test_nonfinite_values_keep_their_class(kind):
+    """NaN stays a NaN (all-ones exponent, nonzero mantissa) and +-Inf stays
+    +-Inf, in both 16-bit formats; FP16 agrees with numpy bit for bit."""
+    v = np.array([np.nan, np.inf, -np.inf])
+    b, ov = oracle.round16(v, kind)
+    mb = 10 if kind == oracle.FP16 else 7
+    exp_ones = (0xFFFF >> (16 - (15 - mb))) << mb & 0x7FFF
+    assert (int(b[0]) & exp_ones) == exp_ones and int(b[0]) & ((1 << mb) - 1) != 0
+    assert int(b[1]) == exp_ones and int(b[2]) == 0x8000 | exp_ones
+    assert ov == 0                                  # none of them was a finite value
+    back = oracle.widen16(b, kind)
+    assert np.isnan(back[0]) and back[1] == np.inf and back[2] == -np.inf
+    if kind == oracle.FP16:
+        assert np.array_equal(b, v.astype(np.float16).view(np.uint16))

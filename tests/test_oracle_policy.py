@@ -48,8 +48,9 @@ def test_conditions_by_hand():
     # C2: many decreases but slow relative decrease
     assert oracle.step_decide(0.1, 5, 0.2, t, P) == 2
     assert oracle.step_decide(0.1, 9, 0.5, t, P) == 0
-    # C3: no decrease at all
+    # C3: no decrease at all; a single decrease is not "no decrease"
     assert oracle.step_decide(0.0, 0, 0.9, t, P) == 4
+    assert oracle.step_decide(0.4, 1, 0.9, t, P) == 0
     # nDec limit replaces t/2 when set
     P2 = oracle.Policy(l=0, t=10, m=1, rsd_limit=0.5, ndec_limit=8, reldec_limit=0.45, max_iter=1)
     assert oracle.step_decide(0.6, 6, 0.9, t, P2) & 1

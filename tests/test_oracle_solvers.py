@@ -196,3 +196,147 @@ def test_floor_trigger_is_silent_when_the_head_is_exact():
     a = oracle.stepped_cg(A.row_ptr, A.col, lv, b, tol=1e-10, policy=_floor_policy(oracle.POLICY_FLOOR))
     c = oracle.stepped_cg(A.row_ptr, A.col, lv, b, tol=1e-10, policy=oracle.SCALED_CG)
     assert a["info"] == c["info"] and np.array_equal(a["x"], c["x"])
+
+
+def test_reported_true_residual_is_recomputed_from_x():
+    """info.rel_res_true is ||b - A x|| / ||b|| for the returned x (dense
+    product in numpy), not the recurrence's estimate."""
+    A = synth.convdiff2d(12, peclet=10.0)
+    D = A.dense()
+    b = synth.rhs_ones(A)
+    nb = np.linalg.norm(b)
+    for out in (oracle.cg(A.row_ptr, A.col, A.val, b, tol=1e-8, max_iter=7),
+                oracle.gmres(A.row_ptr, A.col, A.val, b, tol=1e-8, restart=5, max_iter=12)):
+        assert out["info"]["status"] == oracle.MAXITER
+        assert out["info"]["rel_res_true"] == pytest.approx(np.linalg.norm(b - D @ out["x"]) / nb, rel=1e-10)
+    lv = oracle.levels(A.val)
+    pol = oracle.Policy(l=10 ** 9, t=5, m=5, rsd_limit=0.5, ndec_limit=0, reldec_limit=0.45, max_iter=9)
+    for f in (oracle.stepped_cg, oracle.stepped_gmres):
+        out = f(A.row_ptr, A.col, lv, b, tol=1e-8, policy=pol)
+        r = b - oracle.spmv(A.row_ptr, A.col, lv[2], out["x"])       # measured with A_kmax
+        assert out["info"]["rel_res_true"] == pytest.approx(np.linalg.norm(r) / nb, rel=1e-10)
+
+
+def _always_step(l, t, m, restart, max_iter):
+    # rsd >= 0 > rsd_limit and ndec < ndec_limit always hold: Condition 1
+    # fires at every check, so the step iterations follow from l, t, m alone
+    return oracle.Policy(l=l, t=t, m=m, rsd_limit=-1.0, ndec_limit=10 ** 6, reldec_limit=0.45,
+                         max_iter=max_iter, restart=restart)
+
+
+def test_stepped_cg_check_schedule():
+    """Checks fall at j >= l with j mod m = 0 once t + 1 residuals have been
+    recorded since the last level change; each check raises k by one level.
+    l = 20, m = 10, t = 12: the first check (j = 20, 20 entries) steps to
+    k = 2 and clears the history; j = 30 has 10 entries, too few; j = 40 has 20
+    and steps to k = 3."""
+    A = synth.poisson2d(32)
+    b = synth.rhs_ones(A)
+    lv = oracle.levels(A.val)
+    out = oracle.stepped_cg(A.row_ptr, A.col, lv, b, tol=1e-300, policy=_always_step(20, 12, 10, 30, 60),
+                            hist_cap=100)
+    i = out["info"]
+    assert i["status"] == oracle.MAXITER and i["iters"] == 60 and i["k_final"] == 3
+    assert i["switch_iter"] == [0, 20, 40]
+    # the same policy starting at k = 2 steps once, at the first check
+    p2 = oracle.Policy(**{**_always_step(20, 12, 10, 30, 60).__dict__, "k_start": 2})
+    i2 = oracle.stepped_cg(A.row_ptr, A.col, lv, b, tol=1e-300, policy=p2)["info"]
+    assert i2["switch_iter"] == [-1, 0, 20]
+
+
+def test_stepped_gmres_check_schedule():
+    """GMRES changes level only at a cycle end, and only when the cycle crossed
+    a multiple of m at or after l.  restart 30, l = m = 20, t = 5: cycle 1
+    (j = 30) crossed 20 and steps to k = 2; cycle 2 (j = 60) crossed 40 and 60
+    and steps to k = 3."""
+    A = synth.convdiff2d(24, peclet=10.0)
+    b = synth.rhs_ones(A)
+    lv = oracle.levels(A.val)
+    out = oracle.stepped_gmres(A.row_ptr, A.col, lv, b, tol=1e-300, policy=_always_step(20, 5, 20, 30, 90),
+                               hist_cap=100)
+    i = out["info"]
+    assert i["status"] == oracle.MAXITER and i["iters"] == 90 and i["k_final"] == 3
+    assert i["switch_iter"] == [0, 30, 60]
+    # m = 45: cycle 1 (j = 30) crosses no multiple of 45, cycle 2 (j = 60)
+    # crosses 45, cycle 3 (j = 90) crosses 90
+    i45 = oracle.stepped_gmres(A.row_ptr, A.col, lv, b, tol=1e-300,
+                               policy=_always_step(20, 5, 45, 30, 90))["info"]
+    assert i45["switch_iter"] == [0, 60, 90]
+
+
+def test_plain_solvers_zero_rhs_give_zero():
+    """b = 0: the solution of a nonsingular system is x = 0, whatever x0."""
+    A = synth.poisson2d(6)
+    b = np.zeros(A.n_rows)
+    for out in (oracle.cg(A.row_ptr, A.col, A.val, b, x0=np.ones(A.n_rows)),
+                oracle.gmres(A.row_ptr, A.col, A.val, b, x0=np.ones(A.n_rows))):
+        assert out["info"]["status"] == oracle.OK and out["info"]["iters"] == 0
+        assert np.all(out["x"] == 0)
+
+
+def test_cg_breakdown_on_a_negative_definite_matrix():
+    """p.Ap <= 0 ends plain CG with BREAKDOWN before any update (-A is
+    negative definite, so p_0.A p_0 < 0)."""
+    A = synth.poisson2d(6)
+    b = synth.rhs_ones(A)
+    out = oracle.cg(A.row_ptr, A.col, -A.val, b, max_iter=50)
+    assert out["info"]["status"] == oracle.BREAKDOWN and out["info"]["iters"] == 0
+    assert np.all(out["x"] == 0)
+
+
+def test_breakdown_below_kmax_steps_a_level():
+    """Reading of the stepped solvers: a breakdown at k < k_max raises the
+    level (the truncated operator may have lost definiteness), at k_max it is
+    reported.  The levels are given directly: A_1 = 0 breaks both CG
+    (p.Ap = 0) and GMRES (a zero Hessenberg column) at once, A_1 = -A breaks
+    CG; A_2 = A_3 = A then solve the system from level 2 on."""
+    A = synth.poisson2d(8)
+    b = synth.rhs_ones(A)
+    pol = oracle.Policy(l=10 ** 9, t=5, m=5, rsd_limit=0.5, ndec_limit=0, reldec_limit=0.45, max_iter=500)
+    runs = [(oracle.stepped_cg, 0.0 * A.val), (oracle.stepped_cg, -A.val), (oracle.stepped_gmres, 0.0 * A.val)]
+    for f, a1 in runs:
+        out = f(A.row_ptr, A.col, [a1, A.val, A.val], b, tol=1e-10, policy=pol)
+        i = out["info"]
+        assert i["status"] == oracle.OK and i["switch_iter"][:2] == [0, 0], (f.__name__, i)
+        assert i["rel_res_true"] < 1e-10
+        assert np.max(np.abs(out["x"] - 1.0)) < 1e-8
+        # at k_max the same breakdown is reported
+        bad = f(A.row_ptr, A.col, [a1, a1, a1], b, tol=1e-10, policy=pol)["info"]
+        assert bad["status"] == oracle.BREAKDOWN and bad["k_final"] == 3
+
+
+def test_ok_only_below_tol_in_the_true_residual():
+    """At k_max a recurrence residual below tol is not enough: the true
+    residual decides, and the recurrence restarts from it otherwise.  With a
+    tolerance below the attainable accuracy (1e-18) the recurrence residual
+    keeps falling but the true one cannot, so the solve must not report OK."""
+    A = synth.poisson2d(16)
+    b = synth.rhs_ones(A)
+    lv = oracle.levels(A.val)
+    pol = oracle.Policy(l=10 ** 9, t=5, m=5, rsd_limit=0.5, ndec_limit=0, reldec_limit=0.45, max_iter=400,
+                        k_start=3)
+    for f in (oracle.stepped_cg, oracle.stepped_gmres):
+        out = f(A.row_ptr, A.col, lv, b, tol=1e-18, policy=pol, hist_cap=400)
+        i = out["info"]
+        assert i["status"] == oracle.MAXITER and i["iters"] == 400, (f.__name__, i)
+        assert 1e-18 < i["rel_res_true"] < 1e-13
+        assert np.min(out["hist"]) < 1e-18       # the recurrence went below tol
+
+
+def test_stepped_gmres_history_is_the_least_squares_residual():
+    """The history the stepped GMRES monitors is |g_(i+1)| / ||b||, one entry
+    per inner iteration: it ends at the reported recurrence residual and, in a
+    run without level changes, equals the plain GMRES residual sequence."""
+    A = synth.convdiff2d(12, peclet=10.0)
+    b = synth.rhs_ones(A)
+    lv = oracle.levels(A.val)
+    pol = oracle.Policy(l=10 ** 9, t=5, m=5, rsd_limit=0.5, ndec_limit=0, reldec_limit=0.45, max_iter=45,
+                        restart=15, k_start=3)
+    out = oracle.stepped_gmres(A.row_ptr, A.col, lv, b, tol=1e-14, policy=pol, hist_cap=100)
+    i = out["info"]
+    h = out["hist"]
+    assert i["iters"] == 45 and np.all(h[:45] > 0) and np.all(h[45:] == 0)
+    assert h[44] == i["rel_res_rec"]
+    for c in (15, 30, 45):                    # the plain GMRES stopped after c iterations
+        ref = oracle.gmres(A.row_ptr, A.col, lv[2], b, tol=1e-14, restart=15, max_iter=c)
+        assert ref["info"]["rel_res_rec"] == h[c - 1]

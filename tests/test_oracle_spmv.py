@@ -91,3 +91,23 @@ def test_integer_matrix_times_ones_is_exact():
         y = oracle.gse_spmv(A.row_ptr, A.col, enc, k, ones)
         deg = np.diff(A.row_ptr) - 1
         assert np.array_equal(y, 4.0 - deg)
+
+
+def test_row_scale_is_the_sum_of_absolute_products():
+    """The parity scale sum_j |a_ij x_j| (returned beside Dot2) against exact
+    rational sums: a sum of L nonnegative FP64 products is within
+    gamma_(L+1) of the exact value, and a row with cancelling terms keeps its
+    full magnitude."""
+    rng = np.random.default_rng(7)
+    rp, col, val, dense = _tiny_random(rng, 25, 30, density=0.5)
+    x = rng.uniform(-1, 1, 30)
+    _, ya = oracle.spmv_dot2(rp, col, val, x)
+    for i in range(25):
+        exact = sum(abs(Fraction(float(dense[i, j])) * Fraction(float(x[j]))) for j in range(30))
+        L = int(rp[i + 1] - rp[i])
+        g = (L + 1) * U / (1 - (L + 1) * U)
+        assert abs(Fraction(float(ya[i])) - exact) <= Fraction(g) * exact, i
+    # +a and -a in one row: y = 0, scale = 2|a|
+    y2, ya2 = oracle.spmv_dot2(np.array([0, 2], np.int32), np.array([0, 1], np.int32),
+                               np.array([3.0, -3.0]), np.array([0.5, 0.5]))
+    assert y2[0] == 0.0 and ya2[0] == 3.0
