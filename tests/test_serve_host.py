@@ -23,6 +23,12 @@ def test_footprint_grows_with_size_and_method():
     b = serve.estimate_footprint(100000, 500000)
     assert b > a > 5000 * 10
     assert serve.estimate_footprint(1000, 5000, method="gmres") > a
+    # per extra row at fixed nnz: a row pointer plus the Krylov vectors in FP64,
+    # CG r, p, q, x, b (5) and GMRES(30) its 31 basis vectors, x and b (33)
+    d = 1000
+    for method, vecs in (("cg", 5), ("gmres", 33)):
+        grow = serve.estimate_footprint(1000 + d, 5000, method=method) - serve.estimate_footprint(1000, 5000, method=method)
+        assert grow >= (8 * vecs + 4) * d, method
 
 
 class FakeEngine:
@@ -38,6 +44,8 @@ class FakeEngine:
         self.slots[s] = [self.need[M.rid], M.rid]
         return s
 
+    pending = None
+
     def run(self, nslots, batch=8):
         self.t += nslots
         for v in self.slots.values():
@@ -45,10 +53,16 @@ class FakeEngine:
         return sum(1 for v in self.slots.values() if v[0] > 0)
 
     def launch(self, nslots, batch=8):
-        self.run(nslots, batch)
+        # like the device engine: one launch in flight at a time, its results
+        # visible only after wait()
+        assert self.pending is None, "launch while the previous launch is in flight"
+        self.pending = (nslots, batch)
 
     def wait(self):
-        return sum(1 for v in self.slots.values() if v[0] > 0)
+        assert self.pending is not None, "wait without a launch"
+        nslots, batch = self.pending
+        self.pending = None
+        return self.run(nslots, batch)
 
     def poll(self):
         out = [(s, {"status": 0, "rid": v[1]}) for s, v in self.slots.items() if v[0] <= 0]
@@ -122,6 +136,20 @@ def test_poisson_arrivals_and_shard():
     items = list(range(11))
     parts = [serve.shard(items, r, 3) for r in range(3)]
     assert sorted(sum(parts, [])) == items and all(parts)
+    # round robin, so every rank sees the whole arrival span
+    assert parts == [[0, 3, 6, 9], [1, 4, 7, 10], [2, 5, 8]]
+
+
+def test_latency_runs_from_arrival_to_completion():
+    """Latency is finished - arrival (queueing and encoding included); p50 and
+    p99 by linear interpolation between order statistics: for the latencies
+    1, 2, ..., 101 they are 51 and 100."""
+    done = [serve.Completion(i, arrival=10.0 * i, admitted=10.0 * i + 0.5 * (i + 1), finished=10.0 * i + i + 1,
+                             info={}) for i in range(101)]
+    st = serve.latency_stats(done)
+    assert st["n"] == 101 and st["p50_s"] == pytest.approx(51.0) and st["p99_s"] == pytest.approx(100.0)
+    assert st["mean_s"] == pytest.approx(51.0)
+    assert serve.latency_stats([]) == {"n": 0}
 
 
 def test_longer_steps_only_while_requests_wait():

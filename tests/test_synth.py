@@ -138,3 +138,4 @@ def test_sharding_partitions_the_systems():
     parts = [synth.shard_specs(specs, r, 4) for r in range(4)]
     ids = sorted(id(s) for p in parts for s in p)
     assert ids == sorted(id(s) for s in specs)
+    assert [specs.index(s) for s in parts[1]] == list(range(1, 37, 4))      # round robin
