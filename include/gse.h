@@ -167,10 +167,14 @@ int gse_cg(gse_handle h, const double* b, double* x, double tol, const gse_step_
            gse_solve_info* info, void* stream);
 
 /*
- * Stepped mixed-precision restarted GMRES(restart) (Alg. 3, Sec. III-D;
- * FP64 modified Gram-Schmidt Arnoldi and Givens rotations on the device).  The
- * level changes only at cycle boundaries; the monitored residual is the
- * least-squares residual of each inner iteration.  Arguments as gse_cg.
+ * Stepped mixed-precision restarted GMRES(restart) (Alg. 3, Sec. III-D), in
+ * FP64 on the device: Arnoldi by classical Gram-Schmidt with one conditional
+ * re-orthogonalisation pass (taken when the norm of w falls below 0.7 of its
+ * value before the projection), Givens rotations and the least-squares
+ * residual.  The paper does not name an orthogonalisation; the result equals
+ * modified Gram-Schmidt's up to rounding.  The level changes only at cycle
+ * boundaries; the monitored residual is the least-squares residual of each
+ * inner iteration.  Arguments as gse_cg.
  */
 int gse_gmres(gse_handle h, const double* b, double* x, double tol, const gse_step_policy* policy,
               gse_solve_info* info, void* stream);
@@ -178,8 +182,10 @@ int gse_gmres(gse_handle h, const double* b, double* x, double tol, const gse_st
 /*
  * Batched stepped CG: nsys independent systems (each with its own handle,
  * right-hand side and initial guess) solved concurrently, their kernels
- * interleaved on one stream.  infos: nsys entries (may be NULL).  b and x are
- * host arrays of nsys device pointers.  Returns the first non-OK status.
+ * interleaved on one stream.  The paper solves one system at a time; batching
+ * is a deployment addition, and each system's result is bit-identical to its
+ * solo gse_cg.  infos: nsys entries (may be NULL).  b and x are host arrays of
+ * nsys device pointers.  Returns the first non-OK status.
  */
 int gse_batch_cg(int nsys, const gse_handle* hs, const double* const* b, double* const* x,
                  double tol, const gse_step_policy* policy, gse_solve_info* infos, void* stream);
@@ -193,6 +199,7 @@ int gse_batch_cg(int nsys, const gse_handle* hs, const double* const* b, double*
  * for all of them; gse_engine_poll hands back finished systems and frees their
  * slots.  A handle may occupy at most one slot at a time (its workspace holds
  * the Krylov vectors).  Results of a system do not depend on what else runs.
+ * The paper has no counterpart (it solves one system at a time).
  */
 typedef struct gse_cg_engine* gse_engine;
 int gse_engine_create(int capacity, void* stream, gse_engine* out);
