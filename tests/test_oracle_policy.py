@@ -55,4 +55,3 @@ def test_conditions_by_hand():
     P2 = oracle.Policy(l=0, t=10, m=1, rsd_limit=0.5, ndec_limit=8, reldec_limit=0.45, max_iter=1)
     assert oracle.step_decide(0.6, 6, 0.9, t, P2) & 1
     assert oracle.step_decide(0.1, 8, 0.2, t, P2) == 2
-
