@@ -132,3 +132,16 @@ def test_binding_constants_match_the_header():
     assert len(defs) >= 20
     for name, v in defs.items():
         assert getattr(gse, name) == int(v), name
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    """Without libgse.so every entry of the binding raises: there is no CPU
+    fallback for the GSE path."""
+    import paper_2411_04686_gb300 as gse
+    import synth
+    monkeypatch.setattr(gse, "LIB_PATH", os.path.join(ROOT, "no-such-dir", "libgse.so"))
+    monkeypatch.setattr(gse, "_lib", None)
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        gse.lib()
+    with pytest.raises(RuntimeError):
+        gse.GseMatrix.from_csr(synth.poisson2d(4))
