@@ -58,3 +58,13 @@ def test_peak_comes_from_the_measured_file_when_present():
         assert kind == "measured" and peak == json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
     else:
         assert kind == "fallback"
+
+
+def test_kernels_per_spmv_call():
+    """The row schedule is one kernel; the nonzero split adds the split-row
+    pass once the matrix spans more than one chunk of 256 * schedule nonzeros
+    (the bench's kernel count in the timed region)."""
+    assert bench.spmv_kernels_per_call(8, NNZ128) == 1
+    assert bench.spmv_kernels_per_call(1, 16_140_000) == 2
+    assert bench.spmv_kernels_per_call(4, 1024) == 1 and bench.spmv_kernels_per_call(4, 1025) == 2
+    assert bench.spmv_kernels_per_call(1, 256) == 1
