@@ -44,12 +44,45 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
-# FP64 FMA rate of this GB300 pool, measured by a DFMA throughput kernel
-# (8 independent FMA chains per thread, 2048 threads per SM): 0.59e12 FMA/s.
-DFMA_PEAK_PER_S = 0.59e12
+PEAKS_FILE = os.path.join(ROOT, "profiles", "peaks_gb300.json")
 
 
-GATHER_PEAK_PER_S = 2.45e11   # random 8-byte loads from an 8 MB L2-resident table, measured on this GPU
+def machine_peaks():
+    """The FP64 FMA rate and the random-gather rate that `bench.py --peaks`
+    measured on this GPU pool (profiles/peaks_gb300.json, written by that mode
+    with the command that made it)."""
+    d = json.load(open(PEAKS_FILE))
+    return float(d["dfma_per_s"]), float(d["gather_per_s_8MB"])
+
+
+def run_peaks(args):
+    """Measures the machine floors the SpMV is held against: the FP64 FMA rate
+    (full occupancy, and with a given number of dependent chains per SM), the
+    DFMA latency, and random 8-byte gathers from tables of 8 MB to 1 GB through
+    L1 and L2 only.  Prints one JSON line; with --peaks-out also writes it."""
+    import torch
+    import paper_2411_04686_gb300 as gse
+    torch.cuda.set_device(0)
+    res = {"gpu": torch.cuda.get_device_name(0), "sms": torch.cuda.get_device_properties(0).multi_processor_count}
+    with Clocks(0) as clk:
+        res["dfma_per_s"] = max(gse.probe(gse.PROBE_DFMA_RATE)[0] for _ in range(3))
+        res["dfma_latency_cycles"] = gse.probe(gse.PROBE_DFMA_LATENCY)[0]
+        res["dfma_per_s_by_warps_per_sm"] = {str(w): gse.probe(gse.PROBE_DFMA_CHAINS, w)[0]
+                                             for w in (4, 8, 16, 24, 32, 48, 64)}
+        for mb in (8, 32, 128, 1024):
+            words = mb * 2**20 // 8
+            t = torch.rand(words, dtype=torch.float64, device="cuda")
+            res[f"gather_per_s_{mb}MB"] = max(gse.probe(gse.PROBE_GATHER_L1, words, t)[0] for _ in range(3))
+            res[f"gather_l2only_per_s_{mb}MB"] = max(gse.probe(gse.PROBE_GATHER_L2, words, t)[0] for _ in range(3))
+            del t
+        torch.cuda.synchronize()
+    res["clocks"] = clk.summary()
+    res["command"] = "python bench.py --peaks --peaks-out profiles/peaks_gb300.json"
+    line = json.dumps(res)
+    print(line)
+    if args.peaks_out:
+        with open(args.peaks_out, "w") as f:
+            f.write(json.dumps(res, indent=1) + "\n")
 
 
 def algorithmic_bytes(nnz, n_rows, n_cols, k, seg=(16, 16, 20), G=32):
@@ -72,7 +105,7 @@ def spmv_kernels_per_call(schedule, nnz, rows_schedule=8):
     return 2 if nnz > 256 * schedule else 1
 
 
-SPMV_SOURCES = ("gse_internal.cuh", "spmv_core.cuh", "spmv_pipe.cuh", "spmv.cu")
+SPMV_SOURCES = ("gse_internal.cuh", "spmv_core.cuh", "spmv_lanerow.cuh", "spmv_pipe.cuh", "spmv.cu")
 
 
 def src_hash():
@@ -86,23 +119,59 @@ def src_hash():
 
 
 class Clocks:
-    """Samples SM clocks and throttle reasons with nvidia-smi during a region."""
+    """Samples SM clocks and throttle reasons with nvidia-smi during a region.
+
+    The GPU is named by the UUID of the CUDA device (nvidia-smi numbers GPUs
+    its own way on a shared node).  If the full query is refused, a smaller
+    set of fields is tried; nvidia-smi's error text is kept for the summary."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    Q_OLD = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_throttle_reasons.active,"
+             "clocks_throttle_reasons.hw_slowdown,clocks_throttle_reasons.hw_thermal_slowdown,"
+             "clocks_throttle_reasons.sw_thermal_slowdown,clocks_throttle_reasons.sw_power_cap")
+    Q_MIN = "index,clocks.sm,clocks.max.sm,power.draw"
 
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
+        self.err = ""
+        self.lines = []
+
+    def _gpu_id(self):
+        try:
+            import torch
+            u = str(torch.cuda.get_device_properties(self.gpu).uuid)
+            return u if u.startswith("GPU-") else "GPU-" + u
+        except Exception:                   # noqa: BLE001 -- older torch: fall back to the index
+            return str(self.gpu)
+
+    def _start(self, q):
+        p = subprocess.Popen(["nvidia-smi", f"--id={self._gpu_id()}", f"--query-gpu={q}",
+                              "--format=csv,noheader,nounits", "-lms", "50"],
+                             stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True)
+        first = p.stdout.readline()         # the sampler is running before the region starts
+        if first.strip() and "," in first:
+            return p, first
+        try:
+            _, err = p.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            p.kill()
+            _, err = p.communicate()
+        self.err = (first + " " + (err or "")).strip()[:200]
+        return None, ""
 
     def __enter__(self):
-        try:
-            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "50"],
-                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.first = self.proc.stdout.readline()     # the sampler is running before the region starts
-        except (OSError, FileNotFoundError):
-            self.proc = None
+        for q in (self.Q, self.Q_OLD, self.Q_MIN):
+            try:
+                self.proc, first = self._start(q)
+            except (OSError, FileNotFoundError) as e:
+                self.err = str(e)[:200]
+                self.proc = None
+                break
+            if self.proc:
+                self.first = first
+                break
         return self
 
     def __exit__(self, *a):
@@ -114,27 +183,36 @@ class Clocks:
             except subprocess.TimeoutExpired:
                 self.proc.kill()
                 out, _ = self.proc.communicate()
-            self.lines = [l for l in out.splitlines() if l.strip()]
+            self.lines = [l for l in (self.first + out).splitlines() if l.strip()]
 
     def summary(self):
-        sm, mx, reasons = [], 0.0, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for l in self.lines:
-            f = [x.strip() for x in l.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                sm.append(float(f[1]))
-                mx = max(mx, float(f[2]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, f[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return clock_summary(self.lines, self.err)
+
+
+def clock_summary(lines, err=""):
+    """Median SM clock, maximum clock and the throttle reasons seen in
+    nvidia-smi CSV lines (index, clocks.sm, clocks.max.sm, power.draw and,
+    when queried, the active mask and four reason flags)."""
+    sm, mx, reasons = [], 0.0, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for l in lines:
+        f = [x.strip() for x in l.split(",")]
+        if len(f) < 4:
+            continue
+        try:
+            sm.append(float(f[1]))
+            mx = max(mx, float(f[2]))
+        except ValueError:
+            continue
+        for nm, v in zip(names, f[5:9]):
+            if v.lower().startswith("active"):
+                reasons.add(nm)
+    if not sm:
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        if err:
+            out["error"] = err
+        return out
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
 def build_workload():
@@ -224,7 +302,13 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=10000)
     ap.add_argument("--serve-rates", default="0.5,1,2",
                     help="arrival rates as fractions of the measured saturated batch throughput")
+    ap.add_argument("--peaks", action="store_true",
+                    help="measure the FP64 FMA and random-gather rates (machine probes) and exit")
+    ap.add_argument("--peaks-out", default=None, help="with --peaks: also write the JSON to this file")
     args = ap.parse_args()
+    if args.peaks:
+        run_peaks(args)
+        return
     if args.impl == "reference":
         run_reference(args)
         return
@@ -342,6 +426,7 @@ def main():
     value = bytes_step * world / (ms_step * 1e-3) / 1e9
 
     # per-k table and the dominant kernel's roofline
+    DFMA_PEAK_PER_S, GATHER_PEAK_PER_S = machine_peaks()
     per_k = {}
     for i, (hi, k) in enumerate(launches):
         name, A = handles[hi][0], handles[hi][1]
@@ -373,8 +458,8 @@ def main():
                 "algorithmic_bytes": int(dbytes)}
     if handles[hi][0].startswith("powerlaw"):
         # the random-column matrix is bound by its x gathers, not by HBM: one
-        # 8-byte gather per nonzero at the measured random-gather rate of an
-        # L2-resident 8 MB vector
+        # 8-byte gather per nonzero at the random-gather rate of an L2-resident
+        # 8 MB vector that `bench.py --peaks` measured (profiles/peaks_gb300.json)
         floor_us = dA.nnz / GATHER_PEAK_PER_S * 1e6
         roofline["gather_floor_us"] = round(floor_us, 1)
         roofline["frac_of_gather_floor"] = round(floor_us / (kernel_ms[dom] * 1e3), 3)

@@ -348,6 +348,31 @@ size_t gse_solve_footprint(gse_handle h, int method, int restart);
  * encodes and frees one matrix per request never calls cudaMalloc/cudaFree. */
 void gse_free(gse_handle h);
 
+/* Machine probes (no counterpart in the paper: they measure the GPU the
+ * kernels run on).  On GB300 two floors of the SpMV are not HBM: the FP64 FMA
+ * rate (one DFMA per nonzero) and, for scattered columns, the rate at which
+ * random 8-byte x gathers are served.  gse_probe runs one probe on `stream`
+ * and waits for it; out[0] receives the result, out[1] the kernel time in ms
+ * (where timed):
+ *   GSE_PROBE_DFMA_RATE     FP64 FMAs per second, full occupancy, 8 chains
+ *                           per thread (param unused);
+ *   GSE_PROBE_DFMA_CHAINS   FP64 FMAs per second with `param` warps per SM
+ *                           (1..64), one dependent chain per thread;
+ *   GSE_PROBE_DFMA_LATENCY  SM clock cycles per dependent DFMA, one thread;
+ *   GSE_PROBE_GATHER_L1 /   random 8-byte loads per second from `table`
+ *   GSE_PROBE_GATHER_L2     (device, `param` doubles, a power of two in
+ *                           [2^10, 2^32], owned by the caller), 8 in flight
+ *                           per thread, through L1 (ld.global.nc) or L2 only.
+ * The probe allocates 16 bytes of device scratch per call.  Errors:
+ * GSE_ERR_INVALID (unknown probe, bad param or table), GSE_ERR_OOM,
+ * GSE_ERR_CUDA. */
+#define GSE_PROBE_DFMA_RATE    1
+#define GSE_PROBE_DFMA_CHAINS  2
+#define GSE_PROBE_DFMA_LATENCY 3
+#define GSE_PROBE_GATHER_L1    4
+#define GSE_PROBE_GATHER_L2    5
+int gse_probe(int which, int64_t param, const double* table, double* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

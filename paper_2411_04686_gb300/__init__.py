@@ -29,7 +29,7 @@ EXPORTS = ["gse_strerror", "gse_encode", "gse_attach_values", "gse_spmv", "gse_c
            "gse_engine_poll", "gse_engine_cancel", "gse_engine_destroy", "gse_export", "gse_decode",
            "gse_matrix_get_info", "gse_set_schedule", "gse_autotune", "gse_footprint",
            "gse_solve_footprint", "gse_free", "gse_encode_table", "gse_encode_table_ex", "gse_export_table",
-           "gse_engine_launch", "gse_engine_wait"]
+           "gse_engine_launch", "gse_engine_wait", "gse_probe"]
 
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -119,6 +119,7 @@ def lib():
     L.gse_solve_footprint.restype = ctypes.c_size_t
     L.gse_free.argtypes = [_P]
     L.gse_free.restype = None
+    L.gse_probe.argtypes = [_I, _I64, _P, _P, _P]
     _lib = L
     return L
 
@@ -318,6 +319,17 @@ class GseMatrix:
             self.free()
         except Exception:
             pass
+
+
+PROBE_DFMA_RATE, PROBE_DFMA_CHAINS, PROBE_DFMA_LATENCY, PROBE_GATHER_L1, PROBE_GATHER_L2 = 1, 2, 3, 4, 5
+
+
+def probe(which: int, param: int = 0, table=None, stream=None):
+    """gse_probe: (result, kernel ms) of one machine probe (include/gse.h)."""
+    out = (ctypes.c_double * 2)()
+    _check(lib().gse_probe(which, int(param), None if table is None else _dptr(table), out, _stream_ptr(stream)),
+           "gse_probe")
+    return out[0], out[1]
 
 
 def batch_cg(mats, bs, xs, tol=1e-10, policy: Policy = SCALED_CG, stream=None):

@@ -251,6 +251,18 @@ __global__ void k_row_span(const int32_t* row_ptr, int64_t n, int RB, int* out) 
     }
 }
 
+// Widest slice of a tile of RB consecutive rows that the lane-row kernel
+// stages: from its first nonzero rounded down to 8 to its end rounded up to 8.
+__global__ void k_tile_span(const int32_t* row_ptr, int64_t n, int RB, int* out) {
+    const int64_t nb = (n + RB - 1) / RB;
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r1 = b * RB + RB < n ? b * RB + RB : n;
+        const int64_t s = row_ptr[b * RB], t = row_ptr[r1];
+        const int64_t span = (((t + 7) >> 3) << 3) - ((s >> 3) << 3);
+        atomicMax(out, (int)(span < (1 << 30) ? span : (1 << 30)));
+    }
+}
+
 __global__ void k_block_popc(const uint32_t* rowend, int64_t nblk, int* out) {
     for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nblk; b += (int64_t)gridDim.x * blockDim.x) {
         int s = 0;
@@ -535,7 +547,7 @@ static int encode_impl(const gse_csr* csr, int G, const int* seg_bits, int n_seg
     const int32_t* d_colin = nullptr;
     int32_t* d_colin_own = nullptr;
     const int64_t nflags = n > nblk ? n : nblk;
-    if ((rc = tmp_alloc(&d_err, 8, s)) != GSE_OK) return rc;
+    if ((rc = tmp_alloc(&d_err, 12, s)) != GSE_OK) return rc;
     bool ok = tmp_alloc(&d_flag, nflags + 1, s) == GSE_OK && tmp_alloc(&d_flag2, nflags + 1, s) == GSE_OK &&
               tmp_alloc(&d_pos, nflags + 1, s) == GSE_OK &&
               tmp_alloc(&d_scan_tmp, nflags / SCAN_TILE + 2, s) == GSE_OK &&
@@ -544,7 +556,7 @@ static int encode_impl(const gse_csr* csr, int G, const int* seg_bits, int n_seg
     int status = GSE_OK;
     if (!ok) status = GSE_ERR_OOM;
     if (status == GSE_OK) {
-        cudaMemsetAsync(d_err, 0, 8 * sizeof(int), s);
+        cudaMemsetAsync(d_err, 0, 12 * sizeof(int), s);
         int32_t* rp = (int32_t*)h->buf_row_ptr;
         if (csr->on_device) {
             cudaMemcpyAsync(rp, csr->row_ptr, (n + 1) * sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
@@ -691,12 +703,14 @@ static int encode_impl(const gse_csr* csr, int G, const int* seg_bits, int n_seg
                 }
             }
             if (status == GSE_OK) {
-                cudaMemsetAsync(d_err + 4, 0, 3 * sizeof(int), s);
+                cudaMemsetAsync(d_err + 4, 0, 5 * sizeof(int), s);
                 const int rbs[3] = {32, 128, 256};
                 for (int q = 0; q < 3; q++)
                     if (n > 0) k_row_span<<<grid_for((n + rbs[q] - 1) / rbs[q]), 256, 0, s>>>(rp, n, rbs[q], d_err + 4 + q);
-                int span[3] = {0, 0, 0};
-                cudaMemcpyAsync(span, d_err + 4, 3 * sizeof(int), cudaMemcpyDeviceToHost, s);
+                if (n > 0) k_tile_span<<<grid_for((n + 31) / 32), 256, 0, s>>>(rp, n, 32, d_err + 7);
+                if (n > 0) k_tile_span<<<grid_for((n + 63) / 64), 256, 0, s>>>(rp, n, 64, d_err + 8);
+                int span[5] = {0, 0, 0, 0, 0};
+                cudaMemcpyAsync(span, d_err + 4, 5 * sizeof(int), cudaMemcpyDeviceToHost, s);
                 k_block_popc<<<grid_for(nblk), 256, 0, s>>>((uint32_t*)h->buf_rowend, nblk, d_flag);
                 exclusive_scan(d_flag, nblk, (int*)h->buf_blk_row0, d_scan_tmp, d_total, s);
                 cudaMemsetAsync(h->red_counter, 0, 4 * sizeof(unsigned), s);
@@ -705,6 +719,8 @@ static int encode_impl(const gse_csr* csr, int G, const int* seg_bits, int n_seg
                 h->row_span = span[0];
                 h->row_span128 = span[1];
                 h->row_span256 = span[2];
+                h->tile_span32 = span[3];
+                h->tile_span64 = span[4];
             }
         }
     }

@@ -96,6 +96,8 @@ struct gse_matrix {
     int row_span;        // max nonzeros of any 32-row block, widened to groups of 32
     int row_span128;     // ... of any 128-row block (engine: 4-warp CTAs)
     int row_span256;     // ... of any 256-row block (standalone SpMV: 8-warp CTAs)
+    int tile_span32;     // max nonzeros of any 32-row tile, its ends rounded out to 8 (lane-row stages)
+    int tile_span64;     // ... of any 64-row tile
     int num_exp;         // table format: entries of the exponent table (0: group format)
     int16_t etab_host[64]; // table format: host copy of the table
     int index_in_head;   // table format: 1 when the index sits in the head, 0 in the col word
@@ -175,5 +177,7 @@ struct SpmvArgs {
 };
 
 int launch_spmv(gse_matrix* h, int k, int epi, const SpmvArgs& a, cudaStream_t s, int upl_override = 0);
+// True when gse_spmv at level k runs the lane-row kernel on the row schedule.
+bool lanerow_ok(const gse_matrix* h, int k);
 
 }  // namespace gse

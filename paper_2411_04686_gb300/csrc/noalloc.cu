@@ -117,11 +117,13 @@ extern "C" int gse_cg_noalloc(gse_handle h, const double* b, double* x, double t
     memset(&d, 0, sizeof(d));
     d.m = h->v;
     d.err = h->d_err;
-    sys_partition(d, h, num_sms);
+    sys_partition(d, h, num_sms, pol->k_start, pol->k_max);
     const int64_t nbs = d.nblk_spmv, nbv = d.nblk_vec;
     if (nbs > NA_MAX_BLOCKS || nbv > NA_MAX_BLOCKS) return GSE_ERR_UNSUPPORTED;
     const bool rows = d.sched == GSE_SCHEDULE_ROWS;
-    const size_t p1sm = rows ? p1_rows_smem(d.row_span, d.m.r_lo) : p1_smem();
+    const size_t p1sm = d.lanerow ? (size_t)d.lr_smem
+                        : rows    ? p1_rows_smem(d.row_span, d.m.r_lo)
+                                  : p1_smem();
     d.b = b;
     d.x = x;
     d.r = (double*)(base_ptr + NA_OFF_R);
@@ -169,7 +171,9 @@ extern "C" int gse_cg_noalloc(gse_handle h, const double* b, double* x, double t
     while (used < budget) {
         const int nb = budget - used < 16 ? budget - used : 16;
         for (int it = 0; it < nb; it++) {
-            if (rows) {
+            if (d.lanerow) {
+                k_cg_p1_lr<<<(unsigned)nbs, ENG_LR_WARPS * 32, p1sm, s>>>(d_sys, map_spmv);
+            } else if (rows) {
                 k_cg_p1_rows<<<(unsigned)nbs, ENG_ROW_WARPS * 32, p1sm, s>>>(d_sys, map_spmv);
             } else {
                 k_cg_p1<<<(unsigned)nbs, ENG_WARPS * 32, p1sm, s>>>(d_sys, map_spmv);

@@ -180,6 +180,93 @@ __global__ void __launch_bounds__(ENG_ROW_WARPS * 32, 4) k_cg_p1_rows(const SysD
     p1_body<true>(sys, map, smem, red);
 }
 
+// One lane-row pass as a separate (not inlined) function, so that the
+// p.Ap pass and the residual pass of a kernel get their registers each.
+template <int K, bool DOT, bool RESID>
+__device__ __noinline__ double eng_lr_pass(const MatView& m, const double* x, const Epi& e, int64_t w0, int64_t ws,
+                                           int64_t ntile, unsigned char* wsm) {
+    return lr_loop<K, DOT, RESID, 1>(m, x, e, w0, ws, ntile, wsm);
+}
+
+// Lane-row SpMV phase: warp w of a system's CTAs takes the 32-row tiles w,
+// w + W, ... through its own two-stage ring in shared memory, at the level
+// its system runs.  Each level's pass is a separate function with its own
+// registers; the kernel itself holds little besides the system's matrix
+// view, which it stages in shared memory once per block.
+template <bool ITER>
+__device__ __forceinline__ double eng_lanerow(int k, const MatView& m, const double* x, const Epi& e, int64_t w0,
+                                              int64_t ws, int64_t ntile, unsigned char* smem) {
+    const int warp = threadIdx.x >> 5;
+    switch (k) {
+#define GSE_LR_CASE(KK) \
+    case KK: return eng_lr_pass<KK, ITER, !ITER>(m, x, e, w0, ws, ntile, smem + warp * LR_STAGES * LrLayout<KK, 1>::BYTES);
+        GSE_LR_CASE(1)
+        GSE_LR_CASE(2)
+        GSE_LR_CASE(3)
+        GSE_LR_CASE(SRC_FP32)
+        GSE_LR_CASE(SRC_FP16)
+        GSE_LR_CASE(SRC_BF16)
+        GSE_LR_CASE(SRC_FP64)
+#undef GSE_LR_CASE
+        default: return 0.0;
+    }
+}
+
+__global__ void __launch_bounds__(ENG_LR_WARPS * 32, 4) k_cg_p1_lr(const SysDesc* __restrict__ sys,
+                                                                    const int2* __restrict__ map) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ double red[32];
+    __shared__ MatView mv;
+    const int2 bm = map[blockIdx.x];
+    const SysDesc& S = sys[bm.x];
+    CgState* st = S.st;
+    const int mode = st->mode;
+    if (mode == MODE_DONE) return;
+    const int lb = bm.y, nblk = S.nblk_spmv;
+    static_assert(sizeof(MatView) % 8 == 0, "word copy");
+    if (threadIdx.x < sizeof(MatView) / 8)
+        reinterpret_cast<long long*>(&mv)[threadIdx.x] = reinterpret_cast<const long long*>(&S.m)[threadIdx.x];
+    __syncthreads();
+    Epi e;
+    const double* x;
+    int k;
+    if (mode == MODE_ITER) {
+        e.kind = EPI_CG_PQ; e.y = S.q; e.b = nullptr; e.p = S.p; x = S.p; k = st->k;
+    } else if (mode == MODE_RESID_R) {
+        e.kind = EPI_RESID; e.y = S.r; e.b = S.b; e.p = nullptr; x = S.x; k = st->k;
+    } else {
+        e.kind = EPI_RESID; e.y = S.q; e.b = S.b; e.p = nullptr; x = S.x; k = S.prm.kmax;
+    }
+    const int64_t ntile = (S.n + 31) / 32;      // one row per lane in the engine
+    const int64_t w0 = (int64_t)lb * ENG_LR_WARPS + (threadIdx.x >> 5), ws = (int64_t)nblk * ENG_LR_WARPS;
+    if (mode == MODE_ITER) {
+        const double dot = eng_lanerow<true>(k, mv, x, e, w0, ws, ntile, smem);
+        double total;
+        if (sys_grid_sum(dot, S.partial, S.counter, lb, nblk, red, &total) && threadIdx.x == 0) {
+            const double alpha = st->rho / total;
+            st->pq = total;
+            st->alpha = alpha;
+            st->brk = !(total > 0.0) || !isfinite(total) || !isfinite(alpha);
+        }
+    } else {
+        eng_lanerow<false>(k, mv, x, e, w0, ws, ntile, smem);
+    }
+}
+
+// Dynamic shared memory of the lane-row P1 kernel for systems that run
+// levels up to `widest` (the kernel's limit is set at the engine's creation).
+int p1_lr_occupancy(size_t smem) {
+    cudaFuncSetAttribute((const void*)k_cg_p1_lr, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         lanerow_smem_k<1>(SRC_FP64, ENG_LR_WARPS));
+    int v = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, (const void*)k_cg_p1_lr, ENG_LR_WARPS * 32, smem) !=
+            cudaSuccess || v < 1) {
+        cudaGetLastError();
+        v = 1;
+    }
+    return v;
+}
+
 // ---- P1b: rows that cross chunks (after P1) --------------------------------
 
 __global__ void __launch_bounds__(256) k_cg_fix(const SysDesc* __restrict__ sys, const int2* __restrict__ map) {
@@ -621,7 +708,10 @@ struct gse_cg_engine {
     CgState* h_state = nullptr;    // pinned mirror (latest completed batch)
     CgState* h_stage[2] = {nullptr, nullptr};  // pinned landing buffers, one per batch in flight
     int2* d_map_spmv = nullptr;     // P1 blocks of nonzero-split systems
-    int2* d_map_rows = nullptr;     // P1 blocks of row-schedule systems
+    int2* d_map_rows = nullptr;     // P1 blocks of row-schedule systems (staged row kernel)
+    int2* d_map_lr = nullptr;       // P1 blocks of lane-row systems
+    int map_cap_lr = 0, nblk_lr = 0;
+    size_t lr_smem = 0;             // dynamic shared memory of the lane-row P1 launch (widest system)
     int2* d_map_vec = nullptr;
     int map_cap_spmv = 0, map_cap_rows = 0, map_cap_vec = 0;
     int nblk_spmv = 0, nblk_rows = 0, nblk_vec = 0;
@@ -670,8 +760,9 @@ extern "C" int gse_engine_create(int capacity, void* stream, gse_engine* out) {
     }
     cudaGetDevice(&e->device);
     cudaDeviceGetAttribute(&e->num_sms, cudaDevAttrMultiProcessorCount, e->device);
-    p1_occupancy(false, p1_smem());     // sets both kernels' shared-memory limits
-    p1_occupancy(true, p1_rows_smem_max());
+    p1_occupancy(P1_SPLIT, p1_smem());  // sets the P1 kernels' shared-memory limits on this device
+    p1_occupancy(P1_ROWS, p1_rows_smem_max());
+    p1_lr_occupancy(0);                 // sets the lane-row P1 kernel's shared-memory limit on this device
     e->slots.resize(capacity);
     e->h_sys.resize(capacity);
     if (cudaMalloc(&e->d_sys, capacity * sizeof(SysDesc)) != cudaSuccess ||
@@ -703,6 +794,7 @@ extern "C" void gse_engine_destroy(gse_engine e) {
     if (e->h_stage[1]) cudaFreeHost(e->h_stage[1]);
     if (e->d_map_spmv) cudaFree(e->d_map_spmv);
     if (e->d_map_rows) cudaFree(e->d_map_rows);
+    if (e->d_map_lr) cudaFree(e->d_map_lr);
     if (e->d_map_vec) cudaFree(e->d_map_vec);
     if (e->ev[0]) cudaEventDestroy(e->ev[0]);
     if (e->ev[1]) cudaEventDestroy(e->ev[1]);
@@ -738,7 +830,7 @@ extern "C" int gse_engine_submit(gse_engine e, gse_handle h, const double* b, do
     memset(&d, 0, sizeof(d));
     d.m = h->v;
     d.err = h->d_err;
-    sys_partition(d, h, e->num_sms);
+    sys_partition(d, h, e->num_sms, pol->k_start, pol->k_max);
     if (d.nblk_spmv > w->partial_cap || d.nblk_vec > w->partial_cap) return GSE_ERR_INVALID;
     d.b = b;
     d.x = x;
@@ -785,14 +877,16 @@ extern "C" int gse_engine_submit(gse_engine e, gse_handle h, const double* b, do
 }
 
 static int rebuild_maps(gse_cg_engine* e) {
-    std::vector<int2> ms, mr, mv;
+    std::vector<int2> ms, mr, ml, mv;
     size_t rsm = 0;
+    size_t lsm = 0;
     for (int i = 0; i < e->capacity; i++) {
         if (!e->slots[i].active) continue;
         const SysDesc& d = e->h_sys[i];
-        const bool rows = d.sched == GSE_SCHEDULE_ROWS;
+        const bool rows = d.sched == GSE_SCHEDULE_ROWS && !d.lanerow;
         if (rows && p1_rows_smem(d.row_span, d.m.r_lo) > rsm) rsm = p1_rows_smem(d.row_span, d.m.r_lo);
-        for (int b = 0; b < d.nblk_spmv; b++) (rows ? mr : ms).push_back(make_int2(i, b));
+        if (d.lanerow && (size_t)d.lr_smem > lsm) lsm = (size_t)d.lr_smem;
+        for (int b = 0; b < d.nblk_spmv; b++) (d.lanerow ? ml : rows ? mr : ms).push_back(make_int2(i, b));
         for (int b = 0; b < d.nblk_vec; b++) mv.push_back(make_int2(i, b));
     }
     auto grow = [](int2** buf, int* cap, size_t need) -> int {
@@ -806,13 +900,17 @@ static int rebuild_maps(gse_cg_engine* e) {
     cudaStreamSynchronize(e->stream);
     int rc = grow(&e->d_map_spmv, &e->map_cap_spmv, ms.size());
     if (rc == GSE_OK) rc = grow(&e->d_map_rows, &e->map_cap_rows, mr.size());
+    if (rc == GSE_OK) rc = grow(&e->d_map_lr, &e->map_cap_lr, ml.size());
     if (rc == GSE_OK) rc = grow(&e->d_map_vec, &e->map_cap_vec, mv.size());
     if (rc != GSE_OK) return rc;
     if (!ms.empty()) cudaMemcpy(e->d_map_spmv, ms.data(), ms.size() * sizeof(int2), cudaMemcpyHostToDevice);
     if (!mr.empty()) cudaMemcpy(e->d_map_rows, mr.data(), mr.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    if (!ml.empty()) cudaMemcpy(e->d_map_lr, ml.data(), ml.size() * sizeof(int2), cudaMemcpyHostToDevice);
     if (!mv.empty()) cudaMemcpy(e->d_map_vec, mv.data(), mv.size() * sizeof(int2), cudaMemcpyHostToDevice);
     e->nblk_spmv = (int)ms.size();
     e->nblk_rows = (int)mr.size();
+    e->nblk_lr = (int)ml.size();
+    e->lr_smem = lsm;
     e->nblk_vec = (int)mv.size();
     e->rows_smem = rsm;
     e->dirty = false;
@@ -825,6 +923,8 @@ static int rebuild_maps(gse_cg_engine* e) {
 
 static void enqueue_slots(gse_cg_engine* e, int nslots) {
     for (int it = 0; it < nslots; it++) {
+        if (e->nblk_lr)
+            k_cg_p1_lr<<<e->nblk_lr, ENG_LR_WARPS * 32, e->lr_smem, e->stream>>>(e->d_sys, e->d_map_lr);
         if (e->nblk_rows)
             k_cg_p1_rows<<<e->nblk_rows, ENG_ROW_WARPS * 32, e->rows_smem, e->stream>>>(e->d_sys, e->d_map_rows);
         if (e->nblk_spmv) {

@@ -2,6 +2,7 @@
 // shared with other translation units that launch its kernels.
 #pragma once
 
+#include "spmv_lanerow.cuh"
 #include "spmv_pipe.cuh"
 
 namespace gse {
@@ -12,6 +13,7 @@ constexpr int RING_MAX = 4096;
 constexpr int ENG_WARPS = 4;
 constexpr int ENG_ROW_STAGES = 2;   // stage ring of the row schedule (wide stages: fewer, more CTAs)
 constexpr int ENG_ROW_WARPS = 8;    // row schedule: CTAs of 8 warps, 256-row super-blocks
+constexpr int ENG_LR_WARPS = 8;     // lane-row schedule: CTAs of 8 warps, 64-row tiles per warp
 
 struct CgState {
     int mode, k, status, j, p_action, hlen, hpos, brk;   // brk: p.Ap <= 0 or non-finite (set by P1)
@@ -28,7 +30,10 @@ struct CgParams {
 struct SysDesc {
     MatView m;
     int upl, nblk_spmv, nblk_vec, sched;   // sched: 1 (nonzero split) or GSE_SCHEDULE_ROWS
-    int row_span, pad2;
+    int row_span;              // staged row kernel: 256-row span
+    int lanerow;               // row schedule through the lane-row loop (spmv_lanerow.cuh)
+    int lr_smem;               // lane-row: dynamic shared memory of its P1 CTAs
+    int pad;
     int64_t n, n_chunks;
     const double* b;
     double* x;
@@ -66,6 +71,8 @@ struct Workspace {
 __global__ void k_cg_init(const SysDesc* __restrict__ sys, const int2* __restrict__ map);
 __global__ void k_cg_p1(const SysDesc* __restrict__ sys, const int2* __restrict__ map);        // nonzero split
 __global__ void k_cg_p1_rows(const SysDesc* __restrict__ sys, const int2* __restrict__ map);   // row schedule
+__global__ void k_cg_p1_lr(const SysDesc* __restrict__ sys, const int2* __restrict__ map);     // lane-row schedule
+int p1_lr_occupancy(size_t smem);   // sets the lane-row P1 kernel's shared-memory limit; CTAs per SM at `smem`
 __global__ void k_cg_fix(const SysDesc* __restrict__ sys, const int2* __restrict__ map);
 __global__ void k_cg_p2(const SysDesc* __restrict__ sys, const int2* __restrict__ map);
 __global__ void k_cg_p3(const SysDesc* __restrict__ sys, const int2* __restrict__ map);
@@ -82,16 +89,34 @@ inline size_t p1_rows_smem(int span, int r_lo) {
 }
 inline size_t p1_rows_smem_max() { return p1_rows_smem(GSE_ROW_SPAN_MAX, 16); }
 
-// P1 CTAs an SM holds for a dynamic shared-memory size (row or nonzero-split kernel).
-inline int p1_occupancy(bool rows, size_t smem) {
-    const void* fn = rows ? (const void*)k_cg_p1_rows : (const void*)k_cg_p1;
-    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(rows ? p1_rows_smem_max() : p1_smem()));
+// Shared memory of a lane-row P1 CTA of a system that runs value sources
+// kstart..kmax (GSE levels) or its baseline kmax: the widest of them.
+inline size_t p1_lr_smem(int kstart, int kmax) {
+    int b = 0;
+    if (kmax > 3) b = lanerow_smem_k<1>(kmax, ENG_LR_WARPS);
+    else
+        for (int k = kstart < 1 ? 1 : kstart; k <= kmax; k++) {
+            const int v = lanerow_smem_k<1>(k, ENG_LR_WARPS);
+            b = v > b ? v : b;
+        }
+    return (size_t)b;
+}
+
+// P1 kernels: 0 nonzero split, 1 staged rows, 2 lane-row.
+enum { P1_SPLIT = 0, P1_ROWS = 1, P1_LANEROW = 2 };
+
+// P1 CTAs an SM holds for a dynamic shared-memory size (the kernel's
+// shared-memory limit is set on the current device first).
+inline int p1_occupancy(int which, size_t smem) {
+    const void* fn = which == P1_ROWS ? (const void*)k_cg_p1_rows : (const void*)k_cg_p1;
+    const size_t lim = which == P1_ROWS ? p1_rows_smem_max() : p1_smem();
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim);
+    const int threads = (which == P1_ROWS ? ENG_ROW_WARPS : ENG_WARPS) * 32;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, (rows ? ENG_ROW_WARPS : ENG_WARPS) * 32, smem) !=
-            cudaSuccess ||
-        nb < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, smem) != cudaSuccess || nb < 1) {
+        cudaGetLastError();
         nb = 1;
+    }
     return nb;
 }
 
@@ -100,22 +125,28 @@ inline int p1_occupancy(bool rows, size_t smem) {
 // Block counts depend on the system and the device only, never on what else
 // is in a batch: P1 gets one wave of CTAs at the occupancy of the system's own
 // stage ring (row schedule) or of the nonzero-split ring.
-inline void sys_partition(SysDesc& d, const gse_matrix* h, int num_sms) {
+inline void sys_partition(SysDesc& d, const gse_matrix* h, int num_sms, int kstart, int kmax) {
     d.upl = 1;
-    d.row_span = h->row_span256;   // super-blocks of 32 * ENG_ROW_WARPS = 256 rows
     d.sched = (h->schedule_forced ? h->schedule_forced : h->schedule_auto) == GSE_SCHEDULE_ROWS &&
                       h->row_span256 <= GSE_ROW_SPAN_MAX ? GSE_SCHEDULE_ROWS : 1;
+    d.lanerow = d.sched == GSE_SCHEDULE_ROWS && lanerow_ok(h, kstart) && lanerow_ok(h, kmax) ? 1 : 0;
+    d.row_span = h->row_span256;
+    d.lr_smem = d.lanerow ? (int)p1_lr_smem(kstart, kmax) : 0;
     d.n = h->v.n_rows;
     d.n_chunks = (h->v.nnz + 255) / 256;
     const int64_t partial_cap = (int64_t)num_sms * 64;
     int64_t nbs;
-    if (d.sched == GSE_SCHEDULE_ROWS) {
+    if (d.lanerow) {
+        nbs = (d.n + 32 * ENG_LR_WARPS - 1) / (32 * ENG_LR_WARPS);   // a 32-row tile per warp
+        const int64_t wave = (int64_t)num_sms * p1_lr_occupancy((size_t)d.lr_smem);
+        if (nbs > wave) nbs = wave;
+    } else if (d.sched == GSE_SCHEDULE_ROWS) {
         nbs = (d.n + 32 * ENG_ROW_WARPS - 1) / (32 * ENG_ROW_WARPS);
-        const int64_t wave = (int64_t)num_sms * p1_occupancy(true, p1_rows_smem(d.row_span, d.m.r_lo));
+        const int64_t wave = (int64_t)num_sms * p1_occupancy(P1_ROWS, p1_rows_smem(d.row_span, d.m.r_lo));
         if (nbs > wave) nbs = wave;
     } else {
         nbs = (d.n_chunks + ENG_WARPS - 1) / ENG_WARPS;                // a chunk per warp
-        const int64_t wave = (int64_t)num_sms * p1_occupancy(false, p1_smem());
+        const int64_t wave = (int64_t)num_sms * p1_occupancy(P1_SPLIT, p1_smem());
         if (nbs > wave) nbs = wave;
     }
     if (nbs < 1) nbs = 1;

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <mutex>
 
+#include "spmv_lanerow.cuh"
 #include "spmv_pipe.cuh"
 
 namespace gse {
@@ -60,6 +61,45 @@ __global__ void __launch_bounds__(ROWS_WARPS * 32) k_spmv_rows(MatView m, const 
     spmv_rows_block<K, R, false, RESID, STAGES, TBL>(m, x, e, blockIdx.x, gridDim.x, nsb, L, smem, err);
 }
 
+// Lane-row schedule: one row per lane, two rows per lane in flight, each warp
+// staging its own 64-row tiles (spmv_lanerow.cuh); 8-warp CTAs, warps take
+// tiles round-robin.
+constexpr int LR_WARPS = 8;
+
+template <int K, bool RESID>
+__global__ void __launch_bounds__(LR_WARPS * 32) k_spmv_lanerow(MatView m, const double* __restrict__ x, Epi e,
+                                                                 const int* gate) {
+    if (gate && *gate) return;
+    extern __shared__ __align__(128) unsigned char smem[];
+    constexpr int R = lr_rows_per_lane<K>();
+    const int warp = threadIdx.x >> 5;
+    const int64_t ntile = (m.n_rows + 32 * R - 1) / (32 * R);
+    lr_loop<K, false, RESID>(m, x, e, (int64_t)blockIdx.x * LR_WARPS + warp, (int64_t)gridDim.x * LR_WARPS, ntile,
+                             smem + warp * LR_STAGES * LrLayout<K, R>::BYTES);
+}
+
+typedef void (*LaneRowKernel)(MatView, const double*, Epi, const int*);
+
+template <int K, bool RESID>
+static LaneRowKernel pick_lr(int* smem, int* rows) {
+    *smem = lr_smem<K>(LR_WARPS);
+    *rows = lr_rows_per_lane<K>();
+    return k_spmv_lanerow<K, RESID>;
+}
+
+template <bool RESID>
+static LaneRowKernel pick_lanerow_t(int k, int* smem, int* rows) {
+    switch (k) {
+        case 1: return pick_lr<1, RESID>(smem, rows);
+        case 2: return pick_lr<2, RESID>(smem, rows);
+        case 3: return pick_lr<3, RESID>(smem, rows);
+        case SRC_FP32: return pick_lr<SRC_FP32, RESID>(smem, rows);
+        case SRC_FP16: return pick_lr<SRC_FP16, RESID>(smem, rows);
+        case SRC_BF16: return pick_lr<SRC_BF16, RESID>(smem, rows);
+        default: return pick_lr<SRC_FP64, RESID>(smem, rows);
+    }
+}
+
 typedef void (*RowsKernel)(MatView, const double*, Epi, int64_t, RowStage, int*, const int*);
 
 template <bool RESID, int STAGES>
@@ -84,30 +124,42 @@ static RowsKernel pick_rows_t(int k, int r_lo, RowStage* L, int span, bool tbl) 
     }
 }
 
-// Resident CTAs per SM of a row kernel with its shared memory (0 on error),
-// cached per (kernel, shared-memory size).
-static int rows_resident(RowsKernel fn, size_t smem) {
+// Resident CTAs per SM of a kernel with its block size and dynamic shared
+// memory (0 on error), cached per (kernel, shared-memory size, device): the
+// shared-memory attribute is set on each device before its first launch.
+static int occupancy_cached(const void* fn, int threads, size_t smem) {
     static std::mutex mu;
-    static const void* keys[256];
-    static size_t sizes[256];
-    static int vals[256];
+    static const void* keys[512];
+    static size_t sizes[512];
+    static int devs[512];
+    static int vals[512];
     static int nkeys = 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     std::lock_guard<std::mutex> lock(mu);
     for (int i = 0; i < nkeys; i++)
-        if (keys[i] == (const void*)fn && sizes[i] == smem) return vals[i];
+        if (keys[i] == fn && sizes[i] == smem && devs[i] == dev) return vals[i];
     if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
         return 0;
+    }
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, ROWS_WARPS * 32, smem) != cudaSuccess) return 0;
-    if (nkeys < 256) {
-        keys[nkeys] = (const void*)fn;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (nkeys < 512) {
+        keys[nkeys] = fn;
         sizes[nkeys] = smem;
+        devs[nkeys] = dev;
         vals[nkeys] = nb;
         nkeys++;
     }
     return nb;
 }
+
+static int rows_resident(RowsKernel fn, size_t smem) { return occupancy_cached((const void*)fn, ROWS_WARPS * 32, smem); }
 
 static int launch_rows(gse_matrix* h, int k, int epi, const SpmvArgs& a, cudaStream_t s) {
     RowStage L2, L3;
@@ -135,6 +187,40 @@ static int launch_rows(gse_matrix* h, int k, int epi, const SpmvArgs& a, cudaStr
     e.b = a.b;
     e.p = a.p;
     fn<<<(unsigned)g, ROWS_WARPS * 32, smem, s>>>(h->v, a.x, e, nsb, L, h->d_err, a.skip_flag);
+    return cudaGetLastError() == cudaSuccess ? GSE_OK : GSE_ERR_CUDA;
+}
+
+// The lane-row kernel serves a handle when every tile's slice fits its stage
+// (32-row tiles within 256 nonzeros, 64-row tiles within 512), its rows are at
+// most 64 long, and its level decodes with the lane-row decoders (or is a
+// plain CSR baseline).
+bool lanerow_ok(const gse_matrix* h, int k) {
+    // the table format keeps exponent indices in the column words, which the
+    // lane-row kernel reads as plain columns: that format stays on the other
+    // kernels at every level, its baselines included
+    if (h->v.tbl || h->v.col_mask != 0xFFFFFFFFu) return false;
+    if (h->tile_span32 > lr_cap_rows(1) || h->tile_span64 > lr_cap_rows(2) || h->max_row_len > 64 ||
+        h->v.n_rows >= (int64_t)1 << 30)
+        return false;
+    return k > 3 || lanerow_format(h->v, h->group_size, h->n_seg);
+}
+
+static int launch_lanerow(gse_matrix* h, int k, int epi, const SpmvArgs& a, cudaStream_t s) {
+    int smem = 0, R = 1;
+    LaneRowKernel fn = epi == EPI_RESID ? pick_lanerow_t<true>(k, &smem, &R) : pick_lanerow_t<false>(k, &smem, &R);
+    int nb = occupancy_cached((const void*)fn, LR_WARPS * 32, (size_t)smem);
+    if (nb < 1) nb = 1;
+    const int64_t ntile = (h->v.n_rows + 32 * R - 1) / (32 * R);
+    int64_t g = (ntile + LR_WARPS - 1) / LR_WARPS;
+    const int64_t resident = (int64_t)h->num_sms * nb;
+    if (g > resident) g = resident;
+    if (g < 1) g = 1;
+    Epi e;
+    e.kind = epi;
+    e.y = a.y;
+    e.b = a.b;
+    e.p = a.p;
+    fn<<<(unsigned)g, LR_WARPS * 32, (size_t)smem, s>>>(h->v, a.x, e, a.skip_flag);
     return cudaGetLastError() == cudaSuccess ? GSE_OK : GSE_ERR_CUDA;
 }
 
@@ -226,31 +312,15 @@ static KernelPick pick_kernel(int k, int r_lo, int upl, bool resid, bool tbl) {
     return resid ? pick_kernel_t<true>(k, r_lo, upl) : pick_kernel_t<false>(k, r_lo, upl);
 }
 
-// Occupancy-derived resident blocks per SM for each kernel (cached).
+// Occupancy-derived resident blocks per SM for each kernel (cached per device).
 static int resident_blocks(const KernelPick& kp) {
-    static std::mutex mu;
-    static const void* keys[128];
-    static int vals[128];
-    static int nkeys = 0;
-    std::lock_guard<std::mutex> lock(mu);
-    for (int i = 0; i < nkeys; i++)
-        if (keys[i] == (const void*)kp.fn) return vals[i];
-    if (kp.smem > 48 * 1024)
-        cudaFuncSetAttribute((const void*)kp.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kp.smem);
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kp.fn, kp.warps * 32, kp.smem) != cudaSuccess || nb < 1)
-        nb = 1;
-    if (nkeys < 128) {
-        keys[nkeys] = (const void*)kp.fn;
-        vals[nkeys] = nb;
-        nkeys++;
-    }
-    return nb;
+    const int nb = occupancy_cached((const void*)kp.fn, kp.warps * 32, kp.smem);
+    return nb < 1 ? 1 : nb;
 }
 
 int launch_spmv(gse_matrix* h, int k, int epi, const SpmvArgs& a, cudaStream_t s, int upl_override) {
     int upl = upl_override ? upl_override : units_per_lane(h);
-    if (upl == GSE_SCHEDULE_ROWS) return launch_rows(h, k, epi, a, s);
+    if (upl == GSE_SCHEDULE_ROWS) return lanerow_ok(h, k) ? launch_lanerow(h, k, epi, a, s) : launch_rows(h, k, epi, a, s);
     if (h->v.tbl || src16(k)) upl = 1;         // the table format and the 16-bit baselines run one unit per lane
     const KernelPick kp = pick_kernel(k, h->v.r_lo, upl, epi == EPI_RESID, h->v.tbl != 0);
     const int64_t ch = 256 * upl;

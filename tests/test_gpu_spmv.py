@@ -52,7 +52,26 @@ def _extreme_range():
     return synth.CSR(rp.astype(np.int32), col.astype(np.int32), val, m, "extreme_range")
 
 
+def _band41():
+    """Rows of 41 nonzeros (|i - j| <= 20) with values in [1, 2): one group
+    exponent, rows spanning two or three groups of 32, batches of 8 plus a
+    remainder; n = 1481 is not a multiple of 32."""
+    n = 1481
+    i = np.arange(n)
+    cols = i[:, None] + np.arange(-20, 21)[None, :]
+    valid = (cols >= 0) & (cols < n)
+    vals = 1.0 + ((i[:, None] * 7 + cols * 3) % 11) / 11.0
+    lens = valid.sum(1)
+    rp = np.zeros(n + 1, np.int64)
+    np.cumsum(lens, out=rp[1:])
+    return synth.CSR(rp.astype(np.int32), cols[valid].astype(np.int32), vals[valid], n, "band41")
+
+
 MATS = {
+    # off-diagonals 1e-6 of the diagonal: zero head magnitudes, the leading one
+    # in tail1 (level 2) and tail2 (level 3), one exponent per group
+    "aniso_tiny": lambda: synth.laplace2d(40, 37, shift=0.5, aniso=(1.0, 1e-6)),
+    "band41": _band41,
     "poisson32": lambda: synth.poisson2d(32),
     "extreme_range": _extreme_range,
     "poisson32_third": lambda: synth.poisson2d(32, 1.0 / 3.0),
