@@ -243,7 +243,12 @@ int gse_engine_wait(gse_engine e, int* n_running);
  *    stream capture.
  *  - All calls share the array and each call re-initialises it; calls whose
  *    GPU work overlaps (two threads, two streams) race and corrupt each other.
- * Arguments, results and status codes as gse_cg; the solution equals gse_cg's.
+ * Arguments, results and status codes as gse_cg; the solution, iteration
+ * counts and switch iterations equal gse_cg's bit for bit, and so does
+ * rel_res_true of a converged solve (the true residual both compute on the
+ * device at the convergence check).  For a solve that stops without
+ * converging, rel_res_true is recomputed here by a one-block device sum and
+ * agrees with gse_cg's (a host sum) to rounding only.
  */
 int gse_cg_noalloc(gse_handle h, const double* b, double* x, double tol, const gse_step_policy* policy,
                    gse_solve_info* info, void* stream);
@@ -347,6 +352,19 @@ size_t gse_solve_footprint(gse_handle h, int method, int restart);
  * not returned to the driver before the process exits, so a server that
  * encodes and frees one matrix per request never calls cudaMalloc/cudaFree. */
 void gse_free(gse_handle h);
+
+/* Test hook for the bounded waits (no counterpart in the paper).  The staged
+ * kernels (the 256-row row schedule of the table format and of other segment
+ * layouts, and the 2- and 4-unit nonzero split) wait on shared-memory barriers
+ * for their bulk copies, and every wait gives up after a bounded number of
+ * tries and records GSE_TIMEOUT in the handle, which the next solve on the
+ * handle reports.  With on != 0 these kernels of handle h issue no copy and
+ * wait with a short bound, so each wait runs out at once with nothing in
+ * flight: the path a real expiry takes, without a fault or a hang.  on = 0
+ * restores normal work; each solve starts with the record cleared.  Blocks
+ * until the flag is on the device.  Errors: GSE_ERR_INVALID (NULL handle),
+ * GSE_ERR_CUDA. */
+int gse_test_timeout(gse_handle h, int on);
 
 /* Machine probes (no counterpart in the paper: they measure the GPU the
  * kernels run on).  On GB300 two floors of the SpMV are not HBM: the FP64 FMA

@@ -29,7 +29,7 @@ EXPORTS = ["gse_strerror", "gse_encode", "gse_attach_values", "gse_spmv", "gse_c
            "gse_engine_poll", "gse_engine_cancel", "gse_engine_destroy", "gse_export", "gse_decode",
            "gse_matrix_get_info", "gse_set_schedule", "gse_autotune", "gse_footprint",
            "gse_solve_footprint", "gse_free", "gse_encode_table", "gse_encode_table_ex", "gse_export_table",
-           "gse_engine_launch", "gse_engine_wait", "gse_probe"]
+           "gse_engine_launch", "gse_engine_wait", "gse_probe", "gse_test_timeout"]
 
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -120,6 +120,7 @@ def lib():
     L.gse_free.argtypes = [_P]
     L.gse_free.restype = None
     L.gse_probe.argtypes = [_I, _I64, _P, _P, _P]
+    L.gse_test_timeout.argtypes = [_P, _I]
     _lib = L
     return L
 
@@ -282,6 +283,11 @@ class GseMatrix:
         _check(lib().gse_export_table(self.h, table.ctypes.data, ctypes.byref(n), idx.ctypes.data),
                "gse_export_table")
         return table[: n.value].copy(), idx[: self.nnz]
+
+    def test_timeout(self, on: bool):
+        """gse_test_timeout: the staged kernels of this handle issue no copy and
+        their bounded waits run out at once (test hook)."""
+        _check(lib().gse_test_timeout(self.h, 1 if on else 0), "gse_test_timeout")
 
     def set_schedule(self, upl: int):
         _check(lib().gse_set_schedule(self.h, upl), "gse_set_schedule")

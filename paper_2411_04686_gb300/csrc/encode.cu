@@ -539,6 +539,7 @@ static int encode_impl(const gse_csr* csr, int G, const int* seg_bits, int n_seg
     ALLOC(h->red_counter, unsigned, 4);
     ALLOC(h->red_result, double, 4);
     ALLOC(h->d_err, int, 4);
+    v.inject = h->d_err + 2;     // the timeout test flag (gse_test_timeout), cleared below
     h->bytes_matrix = acc;
     // temporaries
     int *d_err = nullptr, *d_flag = nullptr, *d_flag2 = nullptr, *d_pos = nullptr;

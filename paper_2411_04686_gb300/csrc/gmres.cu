@@ -14,7 +14,8 @@
 #include <cstring>
 #include <vector>
 
-#include "spmv_core.cuh"
+#include "pool.cuh"
+#include "solver_internal.cuh"
 
 namespace gse {
 
@@ -380,9 +381,13 @@ __global__ void k_gm_metrics(GmState* st, const double* ring, int t) {
 
 using namespace gse;
 
+// The GMRES workspace of a handle: the basis V ((restart + 1) n doubles),
+// reduction partials, counters, the residual ring and the device state, kept
+// in the handle (pooled device memory) from its first GMRES solve on, so a
+// solve allocates nothing once a handle has run one of the same or a larger
+// restart length.  gse_free returns it to the pool.
 struct GmWork {
     double* V = nullptr;
-    size_t V_bytes = 0;
     double* partial = nullptr;
     unsigned* counter = nullptr;
     double* ring = nullptr;
@@ -390,13 +395,49 @@ struct GmWork {
     GmState* hst = nullptr;
 };
 
-static void gm_release(GmWork& w) {
-    if (w.V) cudaFree(w.V);
-    if (w.partial) cudaFree(w.partial);
-    if (w.counter) cudaFree(w.counter);
-    if (w.ring) cudaFree(w.ring);
-    if (w.st) cudaFree(w.st);
-    if (w.hst) cudaFreeHost(w.hst);
+static int gm_workspace(gse_matrix* h, int m, int nblk, cudaStream_t s, GmWork* w) {
+    if (!h->ws) h->ws = new Workspace();
+    Workspace* W = h->ws;
+    const int64_t n = h->v.n_rows;
+    if (!W->V || W->V_cols < m + 1) {
+        if (W->V) {
+            cudaStreamSynchronize(s);
+            h->bytes_ws -= (size_t)W->V_cols * (size_t)(n + 2) * sizeof(double);
+            pool_free(W->V);
+            W->V = nullptr;
+            W->V_cols = 0;
+        }
+        if (pool_alloc(&W->V, (size_t)(m + 1) * (size_t)(n + 2), &h->bytes_ws, s) != GSE_OK) return GSE_ERR_OOM;
+        W->V_cols = m + 1;
+    }
+    const size_t scratch = (size_t)(GM_MAX_RESTART + 2) * (size_t)nblk + GM_RING_MAX + 2 * (sizeof(GmState) / 8 + 1) + 8;
+    if (!W->gm_scratch || W->gm_scratch_n < scratch) {
+        if (W->gm_scratch) {
+            cudaStreamSynchronize(s);
+            h->bytes_ws -= W->gm_scratch_n * sizeof(double);
+            pool_free(W->gm_scratch);
+            W->gm_scratch = nullptr;
+            W->gm_scratch_n = 0;
+        }
+        if (pool_alloc(&W->gm_scratch, scratch, &h->bytes_ws, s) != GSE_OK) return GSE_ERR_OOM;
+        W->gm_scratch_n = scratch;
+    }
+    if (!W->gm_host && cudaMallocHost(&W->gm_host, sizeof(GmState)) != cudaSuccess) {
+        cudaGetLastError();
+        W->gm_host = nullptr;
+        return GSE_ERR_OOM;
+    }
+    double* p = W->gm_scratch;
+    w->V = W->V;
+    w->partial = p;
+    p += (size_t)(GM_MAX_RESTART + 2) * (size_t)nblk;
+    w->ring = p;
+    p += GM_RING_MAX;
+    w->st = reinterpret_cast<GmState*>(p);
+    p += sizeof(GmState) / 8 + 1;
+    w->counter = reinterpret_cast<unsigned*>(p);
+    w->hst = static_cast<GmState*>(W->gm_host);
+    return GSE_OK;
 }
 
 static bool level_ok_gm(const gse_matrix* h, int k) { return level_available(h, k); }
@@ -418,16 +459,10 @@ extern "C" int gse_gmres(gse_handle h, const double* b, double* x, double tol, c
     int nblk = h->num_sms * 4;
     const int64_t need = (n + 255) / 256;
     if (nblk > need) nblk = (int)(need < 1 ? 1 : need);
-    if (cudaMalloc(&w.V, (size_t)(m + 1) * n * sizeof(double) + 16) != cudaSuccess ||
-        cudaMalloc(&w.partial, (size_t)(GM_MAX_RESTART + 2) * nblk * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&w.counter, 4 * sizeof(unsigned)) != cudaSuccess ||
-        cudaMalloc(&w.ring, GM_RING_MAX * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&w.st, sizeof(GmState)) != cudaSuccess || cudaMallocHost(&w.hst, sizeof(GmState)) != cudaSuccess) {
-        cudaGetLastError();
-        gm_release(w);
-        return GSE_ERR_OOM;
-    }
+    const int wrc = gm_workspace(h, m, nblk, s, &w);
+    if (wrc != GSE_OK) return wrc;
     cudaMemsetAsync(w.counter, 0, 4 * sizeof(unsigned), s);
+    cudaMemsetAsync(h->d_err, 0, sizeof(int), s);   // this solve's bounded-wait record starts clear
     memset(w.hst, 0, sizeof(GmState));
     w.hst->tol = tol;
     w.hst->nb = 1.0;
@@ -539,7 +574,6 @@ extern "C" int gse_gmres(gse_handle h, const double* b, double* x, double tol, c
         info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     }
     cudaStreamSynchronize(s);
-    gm_release(w);
     int err = 0;
     cudaMemcpy(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost);
     if (err && status != GSE_ERR_CUDA) {

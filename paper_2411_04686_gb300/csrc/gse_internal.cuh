@@ -66,6 +66,7 @@ struct MatView {
     uint32_t col_mask;         // column = col & col_mask
     int hi_shift;              // index in the head: (head >> hi_shift) & hi_mask (hi_mask 0 when not)
     uint32_t hi_mask;
+    const int* inject;         // device flag (gse_test_timeout): staged kernels issue no copy, short waits
     const int16_t* etab;       // the shared exponents (table format; device, 64 entries); with
                                // the index in the head each entry is stored + its bit count, so
                                // the head, read as a full-width head, decodes unchanged

@@ -119,7 +119,7 @@ extern "C" int gse_cg_noalloc(gse_handle h, const double* b, double* x, double t
     d.err = h->d_err;
     sys_partition(d, h, num_sms, pol->k_start, pol->k_max);
     const int64_t nbs = d.nblk_spmv, nbv = d.nblk_vec;
-    if (nbs > NA_MAX_BLOCKS || nbv > NA_MAX_BLOCKS) return GSE_ERR_UNSUPPORTED;
+    if (nbs > NA_MAX_BLOCKS || 2 * nbv > NA_MAX_BLOCKS) return GSE_ERR_UNSUPPORTED;   // P2 keeps two sums per block
     const bool rows = d.sched == GSE_SCHEDULE_ROWS;
     const size_t p1sm = d.lanerow ? (size_t)d.lr_smem
                         : rows    ? p1_rows_smem(d.row_span, d.m.r_lo)
@@ -129,6 +129,7 @@ extern "C" int gse_cg_noalloc(gse_handle h, const double* b, double* x, double t
     d.r = (double*)(base_ptr + NA_OFF_R);
     d.p = (double*)(base_ptr + NA_OFF_P);
     d.q = (double*)(base_ptr + NA_OFF_Q);
+    d.vec2 = vec2_aligned(d.x, d.r, d.p, d.q);
     d.ring = (double*)(base_ptr + NA_OFF_RING);
     d.st = (CgState*)(base_ptr + NA_OFF_STATE);
     d.partial = (double*)(base_ptr + NA_OFF_PARTIAL);
@@ -161,6 +162,7 @@ extern "C" int gse_cg_noalloc(gse_handle h, const double* b, double* x, double t
     cudaMemcpyAsync(d_sys, &d, sizeof(d), cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(d.st, &s0, sizeof(s0), cudaMemcpyHostToDevice, s);
     cudaMemsetAsync(d.counter, 0, 8 * sizeof(unsigned), s);
+    cudaMemsetAsync(h->d_err, 0, sizeof(int), s);   // this solve's bounded-wait record starts clear
     k_na_maps<<<16, 256, 0, s>>>(map_spmv, (int)nbs, map_vec, (int)nbv);
     k_cg_init<<<(unsigned)nbv, 256, 0, s>>>(d_sys, map_vec);
     k_cg_p3<<<(unsigned)nbv, 256, 0, s>>>(d_sys, map_vec);
@@ -187,9 +189,13 @@ extern "C" int gse_cg_noalloc(gse_handle h, const double* b, double* x, double t
         if (cudaStreamSynchronize(s) != cudaSuccess) return GSE_ERR_CUDA;
         if (hs.mode == MODE_DONE) break;
     }
-    // final true residual ||b - A_kmax x|| / ||b|| (q is free now)
+    // final true residual ||b - A_kmax x|| / ||b||: a converged solve's was
+    // computed on the device when it passed the check (x has not changed
+    // since), as gse_cg reports it; otherwise recompute it (q is free now)
     double true_res = 0.0;
-    if (hs.nb > 0.0) {
+    if (hs.mode == MODE_DONE && hs.status == GSE_OK) {
+        true_res = hs.true_res;
+    } else if (hs.nb > 0.0) {
         SpmvArgs a = {};
         a.x = x;
         a.y = d.q;

@@ -61,6 +61,40 @@ __device__ __forceinline__ bool sys_grid_sum(double v, double* partial, unsigned
     return true;
 }
 
+// Two sums at once (partials of the second at partial + nblk).
+__device__ __forceinline__ bool sys_grid_sum2(double v, double w, double* partial, unsigned* counter, int lb,
+                                              int nblk, double* red, double* total_v, double* total_w) {
+    __shared__ bool last;
+    __shared__ double tv, tw;
+    const double s1 = block_sum(v, red);
+    const double s2 = block_sum(w, red);
+    if (threadIdx.x == 0) {
+        partial[lb] = s1;
+        partial[nblk + lb] = s2;
+        __threadfence();
+        last = atomicAdd(counter, 1u) == (unsigned)nblk - 1;
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
+        a += __ldcg(partial + i);
+        b += __ldcg(partial + nblk + i);
+    }
+    a = block_sum(a, red);
+    b = block_sum(b, red);
+    if (threadIdx.x == 0) {
+        tv = a;
+        tw = b;
+        *counter = 0;
+    }
+    __syncthreads();
+    *total_v = tv;
+    *total_w = tw;
+    return true;
+}
+
 // Same block bookkeeping without a sum: true in the last block of the system.
 __device__ __forceinline__ bool sys_grid_last(unsigned* counter, int nblk) {
     __shared__ bool last;
@@ -341,40 +375,72 @@ __global__ void __launch_bounds__(256) k_cg_p2(const SysDesc* __restrict__ sys, 
     if (mode == MODE_DONE) return;
     const int lb = bm.y, nblk = S.nblk_vec;
     const int64_t n = S.n;
-    double acc = 0.0, alpha = 0.0;
+    double acc = 0.0, xacc = 0.0, alpha = 0.0;
     bool brk = false;
+    // the floor rule (GSE_POLICY_FLOOR) compares with ||x_j||, the iterate
+    // after this iteration's update; P3 writes that update as fma(alpha, p, x),
+    // so the same expression here gives its norm exactly
+    const bool floor_rule = (S.prm.flags & GSE_POLICY_FLOOR) != 0;
+    const int64_t t0 = (int64_t)lb * blockDim.x + threadIdx.x, di = (int64_t)nblk * blockDim.x;
     if (mode == MODE_ITER) {
         alpha = st->alpha;
         brk = st->brk != 0;
         if (!brk) {
             double* __restrict__ r = S.r;
             const double* __restrict__ q = S.q;
-            const int64_t di = (int64_t)nblk * blockDim.x;
-            int64_t i = (int64_t)lb * blockDim.x + threadIdx.x;
-            for (; i + 3 * di < n; i += 4 * di) {      // four elements' loads in flight
-                double rv[4], qv[4];
-#pragma unroll
-                for (int u = 0; u < 4; u++) { rv[u] = r[i + u * di]; qv[u] = q[i + u * di]; }
-#pragma unroll
-                for (int u = 0; u < 4; u++) {
-                    const double ri = fma(-alpha, qv[u], rv[u]);
-                    r[i + u * di] = ri;
-                    acc = fma(ri, ri, acc);
+            int64_t i0 = 0;
+            if (S.vec2) {
+                // pairs of elements (16-byte loads), two pairs in flight per thread
+                const int64_t n2 = n >> 1;
+                double2* __restrict__ r2 = reinterpret_cast<double2*>(r);
+                const double2* __restrict__ q2 = reinterpret_cast<const double2*>(q);
+                int64_t i = t0;
+                for (; i + di < n2; i += 2 * di) {
+                    const double2 ra = r2[i], qa = q2[i], rb = r2[i + di], qb = q2[i + di];
+                    const double2 na = make_double2(fma(-alpha, qa.x, ra.x), fma(-alpha, qa.y, ra.y));
+                    const double2 nb = make_double2(fma(-alpha, qb.x, rb.x), fma(-alpha, qb.y, rb.y));
+                    r2[i] = na;
+                    r2[i + di] = nb;
+                    acc = fma(na.x, na.x, acc);
+                    acc = fma(na.y, na.y, acc);
+                    acc = fma(nb.x, nb.x, acc);
+                    acc = fma(nb.y, nb.y, acc);
                 }
+                if (i < n2) {
+                    const double2 ra = r2[i], qa = q2[i];
+                    const double2 na = make_double2(fma(-alpha, qa.x, ra.x), fma(-alpha, qa.y, ra.y));
+                    r2[i] = na;
+                    acc = fma(na.x, na.x, acc);
+                    acc = fma(na.y, na.y, acc);
+                }
+                i0 = 2 * n2;
             }
-            for (; i < n; i += di) {
+            // the scalar loop: every element, or (pairs above) an odd last one
+            const int64_t s0 = S.vec2 ? (t0 == 0 ? i0 : n) : t0;
+            for (int64_t i = s0; i < n; i += di) {
                 const double ri = fma(-alpha, q[i], r[i]);
                 r[i] = ri;
                 acc = fma(ri, ri, acc);
             }
+            if (floor_rule) {
+                const double* __restrict__ x = S.x;
+                const double* __restrict__ p = S.p;
+                for (int64_t i = t0; i < n; i += di) {
+                    const double xi = fma(alpha, p[i], x[i]);
+                    xacc = fma(xi, xi, xacc);
+                }
+            }
         }
     } else {
         const double* __restrict__ v = mode == MODE_RESID_R ? S.r : S.q;
-        for (int64_t i = (int64_t)lb * blockDim.x + threadIdx.x; i < n; i += (int64_t)nblk * blockDim.x)
-            acc = fma(v[i], v[i], acc);
+        for (int64_t i = t0; i < n; i += di) acc = fma(v[i], v[i], acc);
     }
-    double total;
-    if (!sys_grid_sum(acc, S.partial, S.counter + 1, lb, nblk, red, &total)) return;
+    double total, total_x = 0.0;
+    if (floor_rule) {
+        if (!sys_grid_sum2(acc, xacc, S.partial, S.counter + 1, lb, nblk, red, &total, &total_x)) return;
+    } else if (!sys_grid_sum(acc, S.partial, S.counter + 1, lb, nblk, red, &total)) {
+        return;
+    }
     // ---- last block of this system: the decisions ----
     // The state and parameters are brought into shared memory with one
     // parallel load, decided on there, and written back with one parallel
@@ -417,8 +483,8 @@ __global__ void __launch_bounds__(256) k_cg_p2(const SysDesc* __restrict__ sys, 
                     st->mode = MODE_RESID_T;
                 } else {
                     bool step = false;
-                    if (st->k < P.kmax && (P.flags & GSE_POLICY_FLOOR) && st->xnorm2 > 0.0) {
-                        const double floor_k = P.eta[st->k] * sqrt(st->xnorm2) / st->nb;
+                    if (st->k < P.kmax && (P.flags & GSE_POLICY_FLOOR) && total_x > 0.0) {
+                        const double floor_k = P.eta[st->k] * sqrt(total_x) / st->nb;
                         if (res <= floor_k) step = true;
                     }
                     if (!step && st->k < P.kmax && !(P.flags & GSE_POLICY_NO_STAGNATION) && P.m > 0 &&
@@ -484,7 +550,6 @@ __global__ void __launch_bounds__(256) k_cg_p2(const SysDesc* __restrict__ sys, 
 // ---- P3: x and p updates --------------------------------------------------
 
 __global__ void __launch_bounds__(256) k_cg_p3(const SysDesc* __restrict__ sys, const int2* __restrict__ map) {
-    __shared__ double red[32];
     const int2 bm = map[blockIdx.x];
     const SysDesc& S = sys[bm.x];
     CgState* st = S.st;
@@ -497,47 +562,43 @@ __global__ void __launch_bounds__(256) k_cg_p3(const SysDesc* __restrict__ sys, 
     double* __restrict__ p = S.p;
     double* __restrict__ r = S.r;
     const double* __restrict__ q = S.q;
-    double acc = 0.0;
     const int64_t i0 = (int64_t)lb * blockDim.x + threadIdx.x, di = (int64_t)nblk * blockDim.x;
-    // ||x||^2 feeds only the floor rule (GSE_POLICY_FLOOR); FP64 issue is scarce
-    const bool xn = (S.prm.flags & GSE_POLICY_FLOOR) != 0;
-    // the x and p updates, with the ||x||^2 sum only when XN (separate loops,
-    // so no predicated-off FP64 work is issued)
-    auto update = [&](auto XN) {
-        int64_t i = i0;
-        for (; i + 3 * di < n; i += 4 * di) {          // four elements' loads in flight
-            double pv[4], xv[4], rv[4];
-#pragma unroll
-            for (int u = 0; u < 4; u++) { pv[u] = p[i + u * di]; xv[u] = x[i + u * di]; rv[u] = r[i + u * di]; }
-#pragma unroll
-            for (int u = 0; u < 4; u++) {
-                const double xi = fma(alpha, pv[u], xv[u]);
-                x[i + u * di] = xi;
-                p[i + u * di] = fma(beta, pv[u], rv[u]);
-                if constexpr (decltype(XN)::value) acc = fma(xi, xi, acc);
+    if (pa == PA_UPDATE || pa == PA_XONLY) {
+        const bool upd = pa == PA_UPDATE;
+        int64_t j0 = 0;
+        if (S.vec2) {
+            // pairs of elements (16-byte loads), two pairs in flight per thread
+            const int64_t n2 = n >> 1;
+            double2* __restrict__ x2 = reinterpret_cast<double2*>(x);
+            double2* __restrict__ p2 = reinterpret_cast<double2*>(p);
+            const double2* __restrict__ r2 = reinterpret_cast<const double2*>(r);
+            int64_t i = i0;
+            for (; i + di < n2; i += 2 * di) {
+                const double2 pa2 = p2[i], xa = x2[i], pb = p2[i + di], xb = x2[i + di];
+                x2[i] = make_double2(fma(alpha, pa2.x, xa.x), fma(alpha, pa2.y, xa.y));
+                x2[i + di] = make_double2(fma(alpha, pb.x, xb.x), fma(alpha, pb.y, xb.y));
+                if (upd) {
+                    const double2 ra = r2[i], rb = r2[i + di];
+                    p2[i] = make_double2(fma(beta, pa2.x, ra.x), fma(beta, pa2.y, ra.y));
+                    p2[i + di] = make_double2(fma(beta, pb.x, rb.x), fma(beta, pb.y, rb.y));
+                }
             }
+            if (i < n2) {
+                const double2 pa2 = p2[i], xa = x2[i];
+                x2[i] = make_double2(fma(alpha, pa2.x, xa.x), fma(alpha, pa2.y, xa.y));
+                if (upd) {
+                    const double2 ra = r2[i];
+                    p2[i] = make_double2(fma(beta, pa2.x, ra.x), fma(beta, pa2.y, ra.y));
+                }
+            }
+            j0 = 2 * n2;
         }
-        for (; i < n; i += di) {
+        // the scalar loop: every element, or (pairs above) an odd last one
+        for (int64_t i = S.vec2 ? (i0 == 0 ? j0 : n) : i0; i < n; i += di) {
             const double pi = p[i];
-            const double xi = fma(alpha, pi, x[i]);
-            x[i] = xi;
-            p[i] = fma(beta, pi, r[i]);
-            if constexpr (decltype(XN)::value) acc = fma(xi, xi, acc);
+            x[i] = fma(alpha, pi, x[i]);
+            if (upd) p[i] = fma(beta, pi, r[i]);
         }
-    };
-    auto xonly = [&](auto XN) {
-        for (int64_t i = i0; i < n; i += di) {
-            const double xi = fma(alpha, p[i], x[i]);
-            x[i] = xi;
-            if constexpr (decltype(XN)::value) acc = fma(xi, xi, acc);
-        }
-    };
-    if (pa == PA_UPDATE) {
-        if (xn) update(std::true_type{});
-        else update(std::false_type{});
-    } else if (pa == PA_XONLY) {
-        if (xn) xonly(std::true_type{});
-        else xonly(std::false_type{});
     } else if (pa == PA_COPY_R) {
         for (int64_t i = i0; i < n; i += di) p[i] = r[i];
     } else if (pa == PA_COPY_Q) {
@@ -549,16 +610,8 @@ __global__ void __launch_bounds__(256) k_cg_p3(const SysDesc* __restrict__ sys, 
     } else {
         for (int64_t i = i0; i < n; i += di) x[i] = 0.0;
     }
-    double total = 0.0;
-    if (xn) {
-        if (!sys_grid_sum(acc, S.partial, S.counter + 2, lb, nblk, red, &total)) return;
-    } else if (!sys_grid_last(S.counter + 2, nblk)) {
-        return;
-    }
-    if (threadIdx.x == 0) {
-        if (xn && (pa == PA_UPDATE || pa == PA_XONLY)) st->xnorm2 = total;
-        st->p_action = PA_NONE;
-    }
+    if (!sys_grid_last(S.counter + 2, nblk)) return;
+    if (threadIdx.x == 0) st->p_action = PA_NONE;
 }
 
 // ---- P0: ||b|| and the initial state --------------------------------------
@@ -610,6 +663,7 @@ void gse_free_workspace(gse_matrix* h) {
     Workspace* w = h->ws;
     void* bufs[] = {w->r, w->p, w->q, w->ring, w->partial, w->counter, w->V, w->gm_scratch};
     for (void* b : bufs) pool_free(b);
+    if (w->gm_host) cudaFreeHost(w->gm_host);
     delete w;
     h->ws = nullptr;
     h->bytes_ws = 0;
@@ -821,6 +875,7 @@ extern "C" int gse_engine_submit(gse_engine e, gse_handle h, const double* b, do
     engine_enter(e);
     int rc = ensure_cg_workspace(h, e->stream);
     if (rc != GSE_OK) return rc;
+    cudaMemsetAsync(h->d_err, 0, sizeof(int), e->stream);   // this solve's bounded-wait record starts clear
     if ((pol->flags & GSE_POLICY_FLOOR) && !base) {
         rc = compute_eta(h, pol->k_max, e->stream);
         if (rc != GSE_OK) return rc;
@@ -837,6 +892,7 @@ extern "C" int gse_engine_submit(gse_engine e, gse_handle h, const double* b, do
     d.r = w->r;
     d.p = w->p;
     d.q = w->q;
+    d.vec2 = vec2_aligned(d.x, d.r, d.p, d.q);
     d.ring = w->ring;
     d.st = e->d_state + slot;
     d.partial = w->partial;

@@ -18,7 +18,7 @@ constexpr int ENG_LR_WARPS = 8;     // lane-row schedule: CTAs of 8 warps, 64-ro
 struct CgState {
     int mode, k, status, j, p_action, hlen, hpos, brk;   // brk: p.Ap <= 0 or non-finite (set by P1)
     int sw[4];
-    double rho, pq, alpha, beta, nb, res, true_res, xnorm2;
+    double rho, pq, alpha, beta, nb, res, true_res, pad;
 };
 
 struct CgParams {
@@ -33,7 +33,7 @@ struct SysDesc {
     int row_span;              // staged row kernel: 256-row span
     int lanerow;               // row schedule through the lane-row loop (spmv_lanerow.cuh)
     int lr_smem;               // lane-row: dynamic shared memory of its P1 CTAs
-    int pad;
+    int vec2;                  // x, r, p, q 16-byte aligned: the vector phases load element pairs
     int64_t n, n_chunks;
     const double* b;
     double* x;
@@ -60,8 +60,9 @@ struct Workspace {
     // GMRES
     double* V = nullptr;
     int V_cols = 0;
-    double* gm_scratch = nullptr;
+    double* gm_scratch = nullptr;   // GMRES partials, ring, state and counters
     size_t gm_scratch_n = 0;
+    void* gm_host = nullptr;        // pinned host copy of the GMRES state
     bool eta_ready = false;
     double eta[4] = {0, 0, 0, 0};
 };
@@ -125,6 +126,23 @@ inline int p1_occupancy(int which, size_t smem) {
 // Block counts depend on the system and the device only, never on what else
 // is in a batch: P1 gets one wave of CTAs at the occupancy of the system's own
 // stage ring (row schedule) or of the nonzero-split ring.
+// 256-thread CTAs of the vector phases (P2, P3) an SM holds (the smaller).
+inline int vec_occupancy() {
+    int a = 0, b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, (const void*)k_cg_p2, 256, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, (const void*)k_cg_p3, 256, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return 4;
+    }
+    const int v = a < b ? a : b;
+    return v < 1 ? 1 : v;
+}
+
+// True when every vector the vector phases touch is 16-byte aligned.
+inline int vec2_aligned(const void* a, const void* b, const void* c, const void* d) {
+    return (((uintptr_t)a | (uintptr_t)b | (uintptr_t)c | (uintptr_t)d) & 15u) == 0 ? 1 : 0;
+}
+
 inline void sys_partition(SysDesc& d, const gse_matrix* h, int num_sms, int kstart, int kmax) {
     d.upl = 1;
     d.sched = (h->schedule_forced ? h->schedule_forced : h->schedule_auto) == GSE_SCHEDULE_ROWS &&
@@ -150,8 +168,9 @@ inline void sys_partition(SysDesc& d, const gse_matrix* h, int num_sms, int ksta
         if (nbs > wave) nbs = wave;
     }
     if (nbs < 1) nbs = 1;
-    int64_t nbv = (d.n + 1023) / 1024;
-    if (nbv > (int64_t)num_sms * 4) nbv = (int64_t)num_sms * 4;   // fewer partial sums: FP64 adds are scarce
+    int64_t nbv = (d.n + 511) / 512;
+    const int64_t vwave = (int64_t)num_sms * vec_occupancy();      // one wave of the vector phases at most
+    if (nbv > vwave) nbv = vwave;
     if (nbv < 1) nbv = 1;
     if (nbs > partial_cap) nbs = partial_cap;
     if (nbv > partial_cap) nbv = partial_cap;

@@ -361,6 +361,13 @@ extern "C" int gse_spmv(gse_handle h, int k, const double* x, double* y, void* s
     return launch_spmv(h, k, EPI_STORE, a, (cudaStream_t)stream);
 }
 
+extern "C" int gse_test_timeout(gse_handle h, int on) {
+    if (!h || !h->d_err) return GSE_ERR_INVALID;
+    const int v = on ? 1 : 0;
+    if (cudaMemcpy(h->d_err + 2, &v, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) return GSE_ERR_CUDA;
+    return GSE_OK;
+}
+
 extern "C" int gse_set_schedule(gse_handle h, int upl) {
     if (!h || !(upl == 0 || upl == 1 || upl == 2 || upl == 4 || upl == GSE_SCHEDULE_ROWS)) return GSE_ERR_INVALID;
     if (upl == GSE_SCHEDULE_ROWS && (h->row_span256 > GSE_ROW_SPAN_MAX || h->row_span128 > GSE_ROW_SPAN_MAX))

@@ -49,9 +49,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
+// Spin bound of a launch whose handle has the timeout test flag set (no copy
+// is issued, so every wait runs out, quickly, with nothing in flight).
+constexpr uint32_t MBAR_SPIN_TEST = 1024u;
+
 // Bounded wait for phase `parity` of the barrier; false if the bound ran out.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
-    for (uint32_t it = 0; it < MBAR_SPIN_LIMIT; it++)
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, uint32_t limit = MBAR_SPIN_LIMIT) {
+    for (uint32_t it = 0; it < limit; it++)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
@@ -229,6 +233,9 @@ __device__ __forceinline__ double spmv_rows_block(const MatView& m, const double
     unsigned char* stages = smem + 128;
     const bool producer = threadIdx.x == 0;
     const int64_t n = m.n_rows;
+    // test flag (gse_test_timeout): issue no copy, wait with a short bound
+    const bool inj = m.inject && __ldg(m.inject) != 0;
+    const uint32_t lim = inj ? MBAR_SPIN_TEST : MBAR_SPIN_LIMIT;
     double dot = 0.0;
     if (sb0 >= nsb) return dot;
     auto bounds = [&](int64_t sb, int64_t* s0, int64_t* t0) {
@@ -247,7 +254,7 @@ __device__ __forceinline__ double spmv_rows_block(const MatView& m, const double
             mbar_init(smem_u32(empty + s), W);
         }
         fence_mbar_init();
-        for (int s = 0; s < STAGES; s++) {
+        for (int s = 0; s < STAGES && !inj; s++) {
             const int64_t sb = sb0 + s * sbstride;
             if (sb >= nsb) break;
             int64_t bs, bt;
@@ -274,7 +281,7 @@ __device__ __forceinline__ double spmv_rows_block(const MatView& m, const double
             bounds(nxt, &cb_s, &cb_t);
         }
         if (producer && si + sbstride < nsb) bounds(si + sbstride, &is_n, &it_n);
-        ok = __all_sync(FULL, mbar_wait_bounded(smem_u32(full + s), (fphase >> s) & 1u));
+        ok = __all_sync(FULL, mbar_wait_bounded(smem_u32(full + s), (fphase >> s) & 1u, lim));
         if (!ok) break;
         fphase ^= 1u << s;
         const unsigned char* st = stages + s * L.bytes;
@@ -304,7 +311,7 @@ __device__ __forceinline__ double spmv_rows_block(const MatView& m, const double
         if (lane == 0) mbar_arrive(smem_u32(empty + s));      // this warp is done with stage s
         if (producer && si < nsb) {
             // all W warps must have left stage s before it is refilled
-            const bool freed = mbar_wait_bounded(smem_u32(empty + s), (ephase >> s) & 1u);
+            const bool freed = mbar_wait_bounded(smem_u32(empty + s), (ephase >> s) & 1u, lim);
             if (!freed) atomicOr(err, 1);
             else {
                 fence_proxy_async_smem();
@@ -589,6 +596,9 @@ __device__ __forceinline__ double spmv_chunks_block(const MatView& m, const doub
     unsigned char* stages = smem + 128;
     const bool producer = threadIdx.x == 0;
     const int64_t nsc = (nch_total + W - 1) / W;
+    // test flag (gse_test_timeout): issue no copy, wait with a short bound
+    const bool inj = m.inject && __ldg(m.inject) != 0;
+    const uint32_t lim = inj ? MBAR_SPIN_TEST : MBAR_SPIN_LIMIT;
     double dot = 0.0;
     if (sc0 >= nsc) return dot;
     if (producer) {
@@ -597,7 +607,7 @@ __device__ __forceinline__ double spmv_chunks_block(const MatView& m, const doub
             mbar_init(smem_u32(empty + s), W);
         }
         fence_mbar_init();
-        for (int s = 0; s < STAGES; s++) {
+        for (int s = 0; s < STAGES && !inj; s++) {
             const int64_t sc = sc0 + s * scstride;
             if (sc >= nsc) break;
             issue_superchunk<K, R, UPL, TBL>(m, L, sc, nch_total, stages + s * L.bytes, smem_u32(full + s));
@@ -618,7 +628,7 @@ __device__ __forceinline__ double spmv_chunks_block(const MatView& m, const doub
         const ChunkScalars scs = scn;
         const int64_t cn = (sc + scstride) * W + warp;
         if (sc + scstride < nsc && cn < nch_total) scn = chunk_scalars(m, cn, CH, UPL);
-        ok = __all_sync(FULL, mbar_wait_bounded(smem_u32(full + s), (fphase >> s) & 1u));
+        ok = __all_sync(FULL, mbar_wait_bounded(smem_u32(full + s), (fphase >> s) & 1u, lim));
         if (!ok) break;
         fphase ^= 1u << s;
         if (c < nch_total)
@@ -628,7 +638,7 @@ __device__ __forceinline__ double spmv_chunks_block(const MatView& m, const doub
         if (lane == 0) mbar_arrive(smem_u32(empty + s));
         const int64_t si = sc + (int64_t)STAGES * scstride;
         if (producer && si < nsc) {
-            if (!mbar_wait_bounded(smem_u32(empty + s), (ephase >> s) & 1u)) atomicOr(err, 1);
+            if (!mbar_wait_bounded(smem_u32(empty + s), (ephase >> s) & 1u, lim)) atomicOr(err, 1);
             else {
                 fence_proxy_async_smem();
                 issue_superchunk<K, R, UPL, TBL>(m, L, si, nch_total, stages + s * L.bytes, smem_u32(full + s));
