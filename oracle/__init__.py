@@ -26,10 +26,12 @@ POLICY_FLOOR = 2
 
 
 def build(force: bool = False) -> str:
-    """Compiles the oracle into ``oracle/liboracle.so`` (gcc, no OpenMP)."""
+    """Compiles the oracle into ``oracle/liboracle.so`` (gcc; OpenMP only
+    spreads the rows of orc_gse_spmv_rows over threads for the timed CPU
+    baselines, every other routine runs on one thread)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
+        subprocess.check_call(["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
                                "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
@@ -95,6 +97,7 @@ def lib():
         L.orc_spmv.argtypes = [_I64, _P, _P, _P, _P, _P]
         L.orc_spmv.restype = None
         L.orc_gse_spmv.argtypes = [_I64, _P, _P, _P, _P, _P, _P, _I, _P, _I, _I, _P, _P]
+        L.orc_gse_spmv_rows.argtypes = [_I64, _I64, _P, _P, _P, _P, _P, _P, _I, _P, _I, _I, _P, _P, _I]
         L.orc_spmv_dot2.argtypes = [_I64, _P, _P, _P, _P, _P, _P]
         L.orc_spmv_dot2.restype = None
         L.orc_cg.argtypes = [_I64, _P, _P, _P, _P, _P, _D, _I, ctypes.POINTER(Info), _P, _P, _P, _I]
@@ -301,6 +304,22 @@ def gse_spmv(row_ptr, col, enc, k, x, group_size=32, seg_bits=(16, 16, 20)):
                             _ptr(gexp), group_size, _ptr(sb), nseg, k, _ptr(x), _ptr(y))
     if rc != 0:
         raise ValueError(f"orc_gse_spmv status {rc}")
+    return y
+
+
+def gse_spmv_rows(row_ptr, col, enc, k, x, r0, r1, threads=1, y=None, group_size=32, seg_bits=(16, 16, 20)):
+    """gse_spmv over rows [r0, r1) only (y[r0:r1] written), on `threads` host
+    threads; every row is summed as gse_spmv sums it."""
+    row_ptr, col, x = _c(row_ptr, np.int32), _c(col, np.int32), _c(x, np.float64)
+    head, t1, t2, gexp = (_c(enc[0], np.uint16), _c(enc[1], np.uint16), _c(enc[2], np.uint32),
+                          _c(enc[3], np.int16))
+    sb, nseg = _segs(seg_bits)
+    if y is None:
+        y = np.zeros(row_ptr.size - 1, np.float64)
+    rc = lib().orc_gse_spmv_rows(int(r0), int(r1), _ptr(row_ptr), _ptr(col), _ptr(head), _ptr(t1), _ptr(t2),
+                                 _ptr(gexp), group_size, _ptr(sb), nseg, k, _ptr(x), _ptr(y), int(threads))
+    if rc != 0:
+        raise ValueError(f"orc_gse_spmv_rows status {rc}")
     return y
 
 

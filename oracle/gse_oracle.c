@@ -488,6 +488,30 @@ int orc_gse_spmv(int64_t n, const int32_t* row_ptr, const int32_t* col,
     return ORC_OK;
 }
 
+/* The same GSE-SpMV over rows [r0, r1) only (y indexed by row), with the rows
+ * shared among `threads` OpenMP threads when threads > 1.  Every row is summed
+ * exactly as in orc_gse_spmv; only which thread computes it changes.  Used for
+ * the timed CPU baselines (a row sample; all host cores). */
+int orc_gse_spmv_rows(int64_t r0, int64_t r1, const int32_t* row_ptr, const int32_t* col,
+                      const uint16_t* head, const uint16_t* tail1, const uint32_t* tail2,
+                      const int16_t* gexp, int G, const int* seg_bits, int nseg, int k,
+                      const double* x, double* y, int threads)
+{
+    if (total_width(seg_bits, nseg) < 0 || k < 1 || k > nseg || G < 1 || r0 < 0 || r1 < r0 || threads < 1)
+        return ORC_ERR_INVALID;
+#pragma omp parallel for num_threads(threads) schedule(dynamic, 4096) if (threads > 1)
+    for (int64_t i = r0; i < r1; i++) {
+        double s = 0.0;
+        for (int32_t j = row_ptr[i]; j < row_ptr[i + 1]; j++) {
+            double v = decode_one(head[j], k >= 2 ? tail1[j] : 0, k >= 3 ? tail2[j] : 0,
+                                  gexp[j / G], seg_bits, k);
+            s = s + v * x[col[j]];
+        }
+        y[i] = s;
+    }
+    return ORC_OK;
+}
+
 /* Compensated dot product Dot2 (Ogita, Rump, Oishi, "Accurate sum and dot
  * product", SIAM J. Sci. Comput. 26(6), 2005, Algorithm 5.3): TwoProduct by
  * fma, TwoSum (Knuth) for the running sum, error terms summed in FP64.  The

@@ -168,7 +168,7 @@ inline void sys_partition(SysDesc& d, const gse_matrix* h, int num_sms, int ksta
         if (nbs > wave) nbs = wave;
     }
     if (nbs < 1) nbs = 1;
-    int64_t nbv = (d.n + 511) / 512;
+    int64_t nbv = (d.n + 1023) / 1024;
     const int64_t vwave = (int64_t)num_sms * vec_occupancy();      // one wave of the vector phases at most
     if (nbv > vwave) nbv = vwave;
     if (nbv < 1) nbv = 1;

@@ -85,12 +85,18 @@ struct LrLayout {
     static constexpr int BYTES = (OFF_LO + LO_BYTES + 127) / 128 * 128;
 };
 
-// Shared memory of a CTA of W warps: LR_STAGES stages per warp plus a tail pad
-// (a lane past its row reads up to 64 elements beyond the slice; those values
-// are never used, the pad keeps the reads inside the allocation).
+// Shared memory of a CTA of W warps: LR_STAGES stages per warp plus a tail pad.
+// A lane past its row reads up to 63 elements beyond its row (rows are at
+// most 64 long); those values are never used, and the pad keeps the reads of
+// the last stage's last array inside the allocation: 63 values of the widest
+// source (FP64: 504 bytes), else a few nibble words or 16-bit values.
+template <int K>
+__host__ __device__ constexpr int lr_pad() {
+    return K == SRC_FP64 ? 512 : K == SRC_FP32 ? 256 : 128;
+}
 template <int K, int R = lr_rows_per_lane<K>()>
 __host__ __device__ constexpr int lr_smem(int W) {
-    return W * LR_STAGES * LrLayout<K, R>::BYTES + 1024;
+    return W * LR_STAGES * LrLayout<K, R>::BYTES + lr_pad<K>();
 }
 
 // Copies `nc` 16-byte chunks from g to shared address st: lane l takes chunks
@@ -141,28 +147,30 @@ __device__ __forceinline__ uint32_t lr_head_hi(uint32_t h, uint32_t eoff, uint32
     return ((fb >> 3) + eoff) | ((h << 16) & 0x80000000u);
 }
 
-// Fast decode of one value (leading one in the head at K >= 2).  nib: its low
-// tail2 bits (level 3).
+// Fast decode of one value (leading one in the head at K >= 2).  nib16: its
+// low tail2 bits already at bits 16..19 (level 3).
 template <int K>
-__device__ __forceinline__ double lr_fast(uint32_t h, uint32_t t1, uint32_t t2, uint32_t nib, uint32_t eoff) {
-    uint32_t fb;
-    uint32_t hi = lr_head_hi(h, eoff, fb);
-    uint32_t lo = 0;
+__device__ __forceinline__ double lr_fast(uint32_t h, uint32_t t1, uint32_t t2, uint32_t nib16, uint32_t eoff) {
+    const uint32_t fb = __float_as_uint(__uint_as_float(0x4B000000u | (h & 0x7FFFu)) - 8388608.0f);
+    const uint32_t base = (fb >> 3) + eoff;                // exponent and the head's bits below its leading one
+    const uint32_t hs = h << 16;                           // sign at bit 31
+    uint32_t hi, lo = 0;
     if constexpr (K == 1) {
-        hi = (h & 0x7FFFu) ? hi : ((h << 16) & 0x80000000u);
+        hi = (h & 0x7FFFu) ? (base | (hs & 0x80000000u)) : (hs & 0x80000000u);
     } else {
         const uint32_t p = (fb >> 23) - 127u;              // leading one of the head magnitude
+        uint32_t hiT, loT;
         if constexpr (K == 2) {
-            const uint32_t t = t1 << 4;                    // tail1 right below the head bits
-            hi |= t >> p;
-            lo = __funnelshift_r(0u, t, p);
+            hiT = t1 << 4;                                 // tail1 right below the head bits
+            loT = 0;
         } else {
-            // (tail1 << 20 | tail2) << 16, as hiT:loT, then >> p
-            const uint32_t hiT = (t1 << 4) | (t2 >> 12);
-            const uint32_t loT = (t2 << 20) | (nib << 16);
-            hi |= hiT >> p;
-            lo = __funnelshift_r(loT, hiT, p);
+            // (tail1 << 20 | tail2) << 16 as hiT:loT, with W = tail1 << 16 | top 16 bits of tail2
+            const uint32_t W = __byte_perm(t2, t1, 0x5410);
+            hiT = W >> 12;
+            loT = (W << 20) | nib16;
         }
+        hi = ((base | (hiT >> p))) | (hs & 0x80000000u);
+        lo = __funnelshift_r(loT, hiT, p);
     }
     return __hiloint2double((int)hi, (int)lo);
 }
@@ -253,7 +261,9 @@ __device__ __forceinline__ void lr_batch(const MatView& m, const double* __restr
                 const uint32_t nb = (nib[r] >> (4 * u)) & 0xFu;
                 double a;
                 if constexpr (FAST) {
-                    a = lr_fast<K>(h, t1, t2, nb, W.eoff[r]);
+                    // the nibble placed at bits 16..19 with one shift and a mask
+                    const uint32_t nb16 = (4 * u <= 16 ? nib[r] << (16 - 4 * u) : nib[r] >> (4 * u - 16)) & 0xF0000u;
+                    a = lr_fast<K>(h, t1, t2, nb16, W.eoff[r]);
                 } else {
                     const int Eg = u0 + u < W.len[r] ? (int)__ldg(m.gexp + ((W.rs[r] + u0 + u) >> 5)) : 0;
                     a = lr_general<K>(m, h, t1, t2, nb, Eg);

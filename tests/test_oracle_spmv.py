@@ -111,3 +111,19 @@ def test_row_scale_is_the_sum_of_absolute_products():
     y2, ya2 = oracle.spmv_dot2(np.array([0, 2], np.int32), np.array([0, 1], np.int32),
                                np.array([3.0, -3.0]), np.array([0.5, 0.5]))
     assert y2[0] == 0.0 and ya2[0] == 3.0
+
+
+def test_row_range_and_threads_sum_rows_as_the_full_spmv():
+    """orc_gse_spmv_rows (the timed CPU baselines' routine: a row range, rows
+    shared among threads) sums every row exactly as orc_gse_spmv does."""
+    A = synth.powerlaw_random(6000, 16.0, 512, seed=4)
+    x = synth.uniform_x(A.n_cols, seed=2)
+    enc = oracle.encode(A.val)
+    for k in (1, 2, 3):
+        y = oracle.gse_spmv(A.row_ptr, A.col, enc, k, x)
+        for threads in (1, 3):
+            yr = oracle.gse_spmv_rows(A.row_ptr, A.col, enc, k, x, 0, A.n_rows, threads=threads)
+            assert np.array_equal(y.view(np.uint64), yr.view(np.uint64))
+        part = oracle.gse_spmv_rows(A.row_ptr, A.col, enc, k, x, 250, 4100, threads=2)
+        assert np.array_equal(part[250:4100].view(np.uint64), y[250:4100].view(np.uint64))
+        assert not part[:250].any() and not part[4100:].any()
