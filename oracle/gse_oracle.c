@@ -468,23 +468,30 @@ void orc_spmv(int64_t n, const int32_t* row_ptr, const int32_t* col, const doubl
     }
 }
 
-/* GSE-SpMV at level k (Alg. 2 and the two tail variants after it): each value
- * is decoded to FP64 as it is read, then multiplied and accumulated in FP64. */
+/* Row i of the GSE-SpMV at level k (Alg. 2 and the two tail variants after
+ * it): each value is decoded to FP64 as it is read, then multiplied and
+ * accumulated in FP64, left to right. */
+static double gse_row(int64_t i, const int32_t* row_ptr, const int32_t* col,
+                      const uint16_t* head, const uint16_t* tail1, const uint32_t* tail2,
+                      const int16_t* gexp, int G, const int* seg_bits, int k, const double* x)
+{
+    double s = 0.0;
+    for (int32_t j = row_ptr[i]; j < row_ptr[i + 1]; j++) {
+        double v = decode_one(head[j], k >= 2 ? tail1[j] : 0, k >= 3 ? tail2[j] : 0,
+                              gexp[j / G], seg_bits, k);
+        s = s + v * x[col[j]];
+    }
+    return s;
+}
+
+/* GSE-SpMV at level k: y_i = row i for every row. */
 int orc_gse_spmv(int64_t n, const int32_t* row_ptr, const int32_t* col,
                  const uint16_t* head, const uint16_t* tail1, const uint32_t* tail2,
                  const int16_t* gexp, int G, const int* seg_bits, int nseg, int k,
                  const double* x, double* y)
 {
     if (total_width(seg_bits, nseg) < 0 || k < 1 || k > nseg || G < 1) return ORC_ERR_INVALID;
-    for (int64_t i = 0; i < n; i++) {
-        double s = 0.0;
-        for (int32_t j = row_ptr[i]; j < row_ptr[i + 1]; j++) {
-            double v = decode_one(head[j], k >= 2 ? tail1[j] : 0, k >= 3 ? tail2[j] : 0,
-                                  gexp[j / G], seg_bits, k);
-            s = s + v * x[col[j]];
-        }
-        y[i] = s;
-    }
+    for (int64_t i = 0; i < n; i++) y[i] = gse_row(i, row_ptr, col, head, tail1, tail2, gexp, G, seg_bits, k, x);
     return ORC_OK;
 }
 
@@ -500,15 +507,7 @@ int orc_gse_spmv_rows(int64_t r0, int64_t r1, const int32_t* row_ptr, const int3
     if (total_width(seg_bits, nseg) < 0 || k < 1 || k > nseg || G < 1 || r0 < 0 || r1 < r0 || threads < 1)
         return ORC_ERR_INVALID;
 #pragma omp parallel for num_threads(threads) schedule(dynamic, 4096) if (threads > 1)
-    for (int64_t i = r0; i < r1; i++) {
-        double s = 0.0;
-        for (int32_t j = row_ptr[i]; j < row_ptr[i + 1]; j++) {
-            double v = decode_one(head[j], k >= 2 ? tail1[j] : 0, k >= 3 ? tail2[j] : 0,
-                                  gexp[j / G], seg_bits, k);
-            s = s + v * x[col[j]];
-        }
-        y[i] = s;
-    }
+    for (int64_t i = r0; i < r1; i++) y[i] = gse_row(i, row_ptr, col, head, tail1, tail2, gexp, G, seg_bits, k, x);
     return ORC_OK;
 }
 

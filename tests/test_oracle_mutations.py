@@ -71,8 +71,8 @@ MUTANTS = [
      "if (((out[i] >> mb) & ((1 << eb) - 1)) == (1 << eb) - 1) ov++;"),
     # SpMV (Sec. III-C) and the parity scale
     ("gse_spmv_group_of_the_row", S,
-     "                                  gexp[j / G], seg_bits, k);\n            s = s + v * x[col[j]];",
-     "                                  gexp[i / G], seg_bits, k);\n            s = s + v * x[col[j]];"),
+     "                              gexp[j / G], seg_bits, k);\n        s = s + v * x[col[j]];",
+     "                              gexp[i / G], seg_bits, k);\n        s = s + v * x[col[j]];"),
     ("dot2_error_term_dropped", S, "        y[i] = p + s;", "        y[i] = p;"),
     ("dot2_twosum_sign", S, "double q = (p - (q0 - z)) + (h - z);", "double q = (p - (q0 - z)) - (h - z);"),
     ("row_scale_without_abs", S, "sa = sa + fabs(h);", "sa = sa + h;"),
