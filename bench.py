@@ -693,6 +693,19 @@ def main():
         dist.destroy_process_group()
 
 
+def iters_per_level(info):
+    """Iterations run at each level k, from the switch iterations (the
+    iteration at which level k started; -1: never reached)."""
+    sw = list(info["switch_iter"]) + [info["iters"]]
+    out = {}
+    for k in range(len(sw) - 1):
+        if sw[k] < 0:
+            break
+        nxt = next((v for v in sw[k + 1:] if v >= 0), info["iters"])
+        out[f"k{k + 1}"] = nxt - sw[k]
+    return out
+
+
 def solver_comparison(gse, torch):
     """Time-to-1e-10: stepped GSE-CG vs FP64 CSR CG (same fused engine), on the
     3D 7-point Laplacian 192^3 with diagonal shift 1e-3; b = A*1, x0 = 0."""
@@ -700,10 +713,12 @@ def solver_comparison(gse, torch):
     M = gse.GseMatrix.from_csr(A, attach=(64,))
     b = torch.from_numpy(synth.rhs_ones(A)).cuda()
     out = {"workload": "laplace3d_192_shift1e-3_cg_tol1e-10", "n": A.n_rows, "nnz": A.nnz}
-    variants = [("fp64_csr_cg", gse.fp64_policy(gse.SCALED_CG)),
-                ("gse_stepped_cg_paper_policy", gse.SCALED_CG),
-                ("gse_stepped_cg_floor_policy", gse.Policy(**{**gse.SCALED_CG.__dict__, "flags": gse.POLICY_FLOOR}))]
-    for name, pol in variants:
+    variants = [("fp64_csr_cg", "SCALED_CG at FP64", gse.fp64_policy(gse.SCALED_CG)),
+                ("gse_stepped_cg_paper_policy", "SCALED_CG", gse.SCALED_CG),
+                ("gse_stepped_cg_floor_policy", "SCALED_CG + floor rule",
+                 gse.Policy(**{**gse.SCALED_CG.__dict__, "flags": gse.POLICY_FLOOR})),
+                ("gse_stepped_cg_paper_cg_preset", "PAPER_CG (first check at iteration l = 3000)", gse.PAPER_CG)]
+    for name, pname, pol in variants:
         x = torch.zeros(A.n_rows, dtype=torch.float64, device="cuda")
         M.cg(b, x, tol=1e-10, policy=pol)     # warm (workspace, floor coefficients)
         x.zero_()
@@ -713,8 +728,10 @@ def solver_comparison(gse, torch):
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         err = float((x - 1.0).abs().max().item())
-        out[name] = {"seconds": round(dt, 4), "iters": info["iters"], "status": info["status"],
+        out[name] = {"policy": pname, "seconds": round(dt, 4), "iters": info["iters"], "status": info["status"],
                      "k_final": info["k_final"], "switch_iter": info["switch_iter"],
+                     "iters_per_level": iters_per_level(info),
+                     "us_per_iter": round(dt / max(info["iters"], 1) * 1e6, 1),
                      "rel_res_true": info["rel_res_true"], "max_abs_err_vs_ones": err}
     M.free()
     # the same solve on the global-table format (numExp = 8, the paper's setting)
@@ -758,7 +775,8 @@ def solver_comparison(gse, torch):
     out["paper_tolerance_1e-6"] = tol6
     P.free()
     f = out["fp64_csr_cg"]["seconds"]
-    for name in ("gse_stepped_cg_paper_policy", "gse_stepped_cg_floor_policy", "gse_stepped_cg_table8"):
+    for name in ("gse_stepped_cg_paper_policy", "gse_stepped_cg_floor_policy", "gse_stepped_cg_paper_cg_preset",
+                 "gse_stepped_cg_table8"):
         out[name]["speedup_vs_fp64"] = round(f / out[name]["seconds"], 3)
     return out
 

@@ -268,7 +268,9 @@ __device__ __forceinline__ void lr_batch(const MatView& m, const double* __restr
                     const int Eg = u0 + u < W.len[r] ? (int)__ldg(m.gexp + ((W.rs[r] + u0 + u) >> 5)) : 0;
                     a = lr_general<K>(m, h, t1, t2, nb, Eg);
                 }
-                if (u0 + u < W.len[r]) acc[r] = fma(a, xv[r][u], acc[r]);
+                // past the row's end x reads 0 and the fast decoders give a
+                // finite value, so the FMA adds an exact zero (acc is never -0)
+                if (FAST || u0 + u < W.len[r]) acc[r] = fma(a, xv[r][u], acc[r]);
             }
         }
     }

@@ -68,3 +68,9 @@ def test_kernels_per_spmv_call():
     assert bench.spmv_kernels_per_call(1, 16_140_000) == 2
     assert bench.spmv_kernels_per_call(4, 1024) == 1 and bench.spmv_kernels_per_call(4, 1025) == 2
     assert bench.spmv_kernels_per_call(1, 256) == 1
+
+
+def test_iters_per_level_from_switch_iterations():
+    assert bench.iters_per_level({"switch_iter": [0, 50, 80], "iters": 517}) == {"k1": 50, "k2": 30, "k3": 437}
+    assert bench.iters_per_level({"switch_iter": [0, 3000, -1], "iters": 5000}) == {"k1": 3000, "k2": 2000}
+    assert bench.iters_per_level({"switch_iter": [-1, -1, -1], "iters": 471}) == {}
