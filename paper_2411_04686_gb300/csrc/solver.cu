@@ -287,9 +287,74 @@ __global__ void __launch_bounds__(ENG_LR_WARPS * 32, 4) k_cg_p1_lr(const SysDesc
     }
 }
 
+// The p.Ap pass of one system whose matrix view is the kernel's parameter:
+// every level's loop inlined, so the view's fields are read from the
+// parameter bank as in the standalone SpMV kernel, not from registers.
+__device__ __forceinline__ double solo_lr_iter(int k, const MatView& m, const double* x, const Epi& e, int64_t w0,
+                                               int64_t ws, int64_t ntile, unsigned char* smem) {
+    const int warp = threadIdx.x >> 5;
+    switch (k) {
+#define GSE_LR_SOLO(KK) \
+    case KK: return lr_loop<KK, true, false, 1>(m, x, e, w0, ws, ntile, smem + warp * LR_STAGES * LrLayout<KK, 1>::BYTES);
+        GSE_LR_SOLO(1)
+        GSE_LR_SOLO(2)
+        GSE_LR_SOLO(3)
+        GSE_LR_SOLO(SRC_FP32)
+        GSE_LR_SOLO(SRC_FP16)
+        GSE_LR_SOLO(SRC_BF16)
+        GSE_LR_SOLO(SRC_FP64)
+#undef GSE_LR_SOLO
+        default: return 0.0;
+    }
+}
+
+// k_cg_p1_lr for an engine that holds one lane-row system: the same
+// partition (grid = the system's P1 blocks, block b = its block b), the same
+// passes and the same sums, so its results are bit-identical; only the
+// matrix view travels as a launch parameter.  The residual passes (a few per
+// solve) take the shared-memory copy and the separate pass functions.
+__global__ void __launch_bounds__(ENG_LR_WARPS * 32, 4) k_cg_p1_lr_solo(const __grid_constant__ MatView m,
+                                                                         const SysDesc* __restrict__ sys) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ double red[32];
+    __shared__ MatView mv;
+    const SysDesc& S = *sys;
+    CgState* st = S.st;
+    const int mode = st->mode;
+    if (mode == MODE_DONE) return;
+    const int lb = blockIdx.x, nblk = S.nblk_spmv;
+    const int64_t ntile = (S.n + 31) / 32;
+    const int64_t w0 = (int64_t)lb * ENG_LR_WARPS + (threadIdx.x >> 5), ws = (int64_t)nblk * ENG_LR_WARPS;
+    Epi e;
+    if (mode == MODE_ITER) {
+        e.kind = EPI_CG_PQ; e.y = S.q; e.b = nullptr; e.p = S.p;
+        const double dot = solo_lr_iter(st->k, m, S.p, e, w0, ws, ntile, smem);
+        double total;
+        if (sys_grid_sum(dot, S.partial, S.counter, lb, nblk, red, &total) && threadIdx.x == 0) {
+            const double alpha = st->rho / total;
+            st->pq = total;
+            st->alpha = alpha;
+            st->brk = !(total > 0.0) || !isfinite(total) || !isfinite(alpha);
+        }
+        return;
+    }
+    if (threadIdx.x < sizeof(MatView) / 8)
+        reinterpret_cast<long long*>(&mv)[threadIdx.x] = reinterpret_cast<const long long*>(&m)[threadIdx.x];
+    __syncthreads();
+    int k;
+    if (mode == MODE_RESID_R) {
+        e.kind = EPI_RESID; e.y = S.r; e.b = S.b; e.p = nullptr; k = st->k;
+    } else {
+        e.kind = EPI_RESID; e.y = S.q; e.b = S.b; e.p = nullptr; k = S.prm.kmax;
+    }
+    eng_lanerow<false>(k, mv, S.x, e, w0, ws, ntile, smem);
+}
+
 // Dynamic shared memory of the lane-row P1 kernel for systems that run
 // levels up to `widest` (the kernel's limit is set at the engine's creation).
 int p1_lr_occupancy(size_t smem) {
+    cudaFuncSetAttribute((const void*)k_cg_p1_lr_solo, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         lanerow_smem_k<1>(SRC_FP64, ENG_LR_WARPS));
     cudaFuncSetAttribute((const void*)k_cg_p1_lr, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          lanerow_smem_k<1>(SRC_FP64, ENG_LR_WARPS));
     int v = 0;
@@ -765,6 +830,7 @@ struct gse_cg_engine {
     int2* d_map_rows = nullptr;     // P1 blocks of row-schedule systems (staged row kernel)
     int2* d_map_lr = nullptr;       // P1 blocks of lane-row systems
     int map_cap_lr = 0, nblk_lr = 0;
+    int solo_lr = -1;               // the slot, when the lane-row blocks all belong to one system
     size_t lr_smem = 0;             // dynamic shared memory of the lane-row P1 launch (widest system)
     int2* d_map_vec = nullptr;
     int map_cap_spmv = 0, map_cap_rows = 0, map_cap_vec = 0;
@@ -966,6 +1032,7 @@ static int rebuild_maps(gse_cg_engine* e) {
     e->nblk_spmv = (int)ms.size();
     e->nblk_rows = (int)mr.size();
     e->nblk_lr = (int)ml.size();
+    e->solo_lr = !ml.empty() && ml.front().x == ml.back().x ? ml.front().x : -1;
     e->lr_smem = lsm;
     e->nblk_vec = (int)mv.size();
     e->rows_smem = rsm;
@@ -979,7 +1046,10 @@ static int rebuild_maps(gse_cg_engine* e) {
 
 static void enqueue_slots(gse_cg_engine* e, int nslots) {
     for (int it = 0; it < nslots; it++) {
-        if (e->nblk_lr)
+        if (e->nblk_lr && e->solo_lr >= 0)
+            k_cg_p1_lr_solo<<<e->nblk_lr, ENG_LR_WARPS * 32, e->lr_smem, e->stream>>>(e->h_sys[e->solo_lr].m,
+                                                                                     e->d_sys + e->solo_lr);
+        else if (e->nblk_lr)
             k_cg_p1_lr<<<e->nblk_lr, ENG_LR_WARPS * 32, e->lr_smem, e->stream>>>(e->d_sys, e->d_map_lr);
         if (e->nblk_rows)
             k_cg_p1_rows<<<e->nblk_rows, ENG_ROW_WARPS * 32, e->rows_smem, e->stream>>>(e->d_sys, e->d_map_rows);
