@@ -828,8 +828,9 @@ def gmres_comparison(gse, torch):
 def batched_comparison(gse, torch, nsys, rank, world):
     """nsys SPD systems of uneven size (n log-uniform 1e3..2.56e5, 2D/3D
     anisotropic Laplacians with a diagonal shift) solved to 1e-10 in one
-    continuous batch; FP64 CSR in the same batched engine, and FP64 CSR CG one
-    system at a time (a sample of 32 systems, scaled)."""
+    continuous batch: stepped GSE-CG under the scaled policy, the same with the
+    perturbation-floor trigger added, FP64 CSR in the same batched engine, and
+    FP64 CSR CG one system at a time (a sample of 32 systems, scaled)."""
     specs = synth.shard_specs(synth.batch_specs(nsys, seed=0), rank, world) if world > 1 else synth.batch_specs(nsys, seed=0)
     t0 = time.perf_counter()
     As = [sp.build() for sp in specs]
@@ -843,8 +844,13 @@ def batched_comparison(gse, torch, nsys, rank, world):
            "systems": len(As), "total_rows": int(sum(A.n_rows for A in As)),
            "total_nnz": int(sum(A.nnz for A in As)), "host_generate_s": round(t_gen, 2),
            "encode_s": round(t_enc, 3)}
-    for name, pol in (("gse_stepped_batched", gse.SCALED_CG), ("fp64_csr_batched", gse.fp64_policy(gse.SCALED_CG))):
+    floor = gse.Policy(**{**gse.SCALED_CG.__dict__, "flags": gse.POLICY_FLOOR})
+    for name, pol in (("gse_stepped_batched", gse.SCALED_CG), ("gse_stepped_batched_floor", floor),
+                      ("fp64_csr_batched", gse.fp64_policy(gse.SCALED_CG))):
         xs = [torch.zeros(A.n_rows, dtype=torch.float64, device="cuda") for A in As]
+        gse.batch_cg(mats, bs, xs, tol=1e-10, policy=pol)     # warm (workspaces, floor coefficients)
+        for x in xs:
+            x.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         rc, infos = gse.batch_cg(mats, bs, xs, tol=1e-10, policy=pol)
@@ -861,6 +867,8 @@ def batched_comparison(gse, torch, nsys, rank, world):
         out[name] = {"seconds": round(dt, 4), "solves_per_s": round(nsolved / dt, 2), "status": rc,
                      "all_converged": all(i["status"] == gse.OK for i in infos),
                      "max_iters": max(i["iters"] for i in infos),
+                     # sum over systems of rows x iterations: the work the batch does
+                     "row_iters": int(sum(A.n_rows * i["iters"] for A, i in zip(As, infos))),
                      "max_rel_res_true": max(i["rel_res_true"] for i in infos)}
     idx = list(range(0, len(As), max(1, len(As) // 32)))[:32]
     t_single = 0.0
@@ -875,6 +883,10 @@ def batched_comparison(gse, torch, nsys, rank, world):
     out["fp64_csr_one_at_a_time"] = {"seconds_estimated": round(est, 3), "sampled_systems": len(idx),
                                      "solves_per_s": round(len(As) / est, 2)}
     out["speedup_batched_gse_vs_one_at_a_time_fp64"] = round(est / out["gse_stepped_batched"]["seconds"], 2)
+    for name in ("gse_stepped_batched", "gse_stepped_batched_floor"):
+        g, f = out[name], out["fp64_csr_batched"]
+        g["speedup_vs_fp64_batched"] = round(f["seconds"] / g["seconds"], 3)
+        g["row_iters_vs_fp64"] = round(g["row_iters"] / f["row_iters"], 3)
     for M in mats:
         M.free()
     return out

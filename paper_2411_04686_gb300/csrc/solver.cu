@@ -12,7 +12,9 @@
 //                             convergence check and the next mode
 //                    RESID_R: rho = r.r      RESID_T: ||q||, decide
 //   P3  vector 2     x += alpha p (the x update is folded here, one pass) and
-//                    p = r + beta p, or p = r / r = p = q after a restart
+//                    p = r + beta p, or p = r / r = p = q after a restart;
+//                    under the floor rule also ||x_j|| and (last block) the
+//                    floor decision
 // The host only enqueues slots (batches of them replayed from a captured CUDA
 // graph) and reads the state array once per batch, so a single solve runs
 // without a host round trip per iteration, and a batch of systems shares each
@@ -440,12 +442,8 @@ __global__ void __launch_bounds__(256) k_cg_p2(const SysDesc* __restrict__ sys, 
     if (mode == MODE_DONE) return;
     const int lb = bm.y, nblk = S.nblk_vec;
     const int64_t n = S.n;
-    double acc = 0.0, xacc = 0.0, alpha = 0.0;
+    double acc = 0.0, alpha = 0.0;
     bool brk = false;
-    // the floor rule (GSE_POLICY_FLOOR) compares with ||x_j||, the iterate
-    // after this iteration's update; P3 writes that update as fma(alpha, p, x),
-    // so the same expression here gives its norm exactly
-    const bool floor_rule = (S.prm.flags & GSE_POLICY_FLOOR) != 0;
     const int64_t t0 = (int64_t)lb * blockDim.x + threadIdx.x, di = (int64_t)nblk * blockDim.x;
     if (mode == MODE_ITER) {
         alpha = st->alpha;
@@ -487,25 +485,13 @@ __global__ void __launch_bounds__(256) k_cg_p2(const SysDesc* __restrict__ sys, 
                 r[i] = ri;
                 acc = fma(ri, ri, acc);
             }
-            if (floor_rule) {
-                const double* __restrict__ x = S.x;
-                const double* __restrict__ p = S.p;
-                for (int64_t i = t0; i < n; i += di) {
-                    const double xi = fma(alpha, p[i], x[i]);
-                    xacc = fma(xi, xi, xacc);
-                }
-            }
         }
     } else {
         const double* __restrict__ v = mode == MODE_RESID_R ? S.r : S.q;
         for (int64_t i = t0; i < n; i += di) acc = fma(v[i], v[i], acc);
     }
-    double total, total_x = 0.0;
-    if (floor_rule) {
-        if (!sys_grid_sum2(acc, xacc, S.partial, S.counter + 1, lb, nblk, red, &total, &total_x)) return;
-    } else if (!sys_grid_sum(acc, S.partial, S.counter + 1, lb, nblk, red, &total)) {
-        return;
-    }
+    double total;
+    if (!sys_grid_sum(acc, S.partial, S.counter + 1, lb, nblk, red, &total)) return;
     // ---- last block of this system: the decisions ----
     // The state and parameters are brought into shared memory with one
     // parallel load, decided on there, and written back with one parallel
@@ -547,17 +533,12 @@ __global__ void __launch_bounds__(256) k_cg_p2(const SysDesc* __restrict__ sys, 
                 } else if (res < P.tol) {
                     st->mode = MODE_RESID_T;
                 } else {
-                    bool step = false;
-                    if (st->k < P.kmax && (P.flags & GSE_POLICY_FLOOR) && total_x > 0.0) {
-                        const double floor_k = P.eta[st->k] * sqrt(total_x) / st->nb;
-                        if (res <= floor_k) step = true;
-                    }
-                    if (!step && st->k < P.kmax && !(P.flags & GSE_POLICY_NO_STAGNATION) && P.m > 0 &&
+                    // the floor rule (GSE_POLICY_FLOOR) is decided in P3, which
+                    // forms x_j; every outcome decided here leaves it to P3
+                    if (st->k < P.kmax && !(P.flags & GSE_POLICY_NO_STAGNATION) && P.m > 0 &&
                         st->j >= P.l && st->j % P.m == 0 && st->hlen >= cap)
                         need_metrics = 1;
-                    if (step) {
-                        step_level(st); st->mode = MODE_RESID_R;
-                    } else if (!need_metrics) {
+                    if (!need_metrics) {
                         if (st->j >= P.max_iter) {
                             st->mode = MODE_DONE; st->status = GSE_MAXITER;
                         } else {
@@ -623,6 +604,15 @@ __global__ void __launch_bounds__(256) k_cg_p3(const SysDesc* __restrict__ sys, 
     const int lb = bm.y, nblk = S.nblk_vec;
     const int64_t n = S.n;
     const double alpha = st->alpha, beta = st->beta;
+    // The floor rule (GSE_POLICY_FLOOR, checked before the stagnation test in
+    // the iteration's order) compares res_j with eta_k ||x_j|| / ||b||, x_j the
+    // iterate this pass stores.  It is due when P2 let the iteration continue
+    // (p is updated) or stopped it at max_iter; a stagnation step, a
+    // convergence check or a breakdown decided in P2 comes first.  Uniform
+    // over the system's blocks (all read the same state).
+    const bool floor_due = (S.prm.flags & GSE_POLICY_FLOOR) && st->k < S.prm.kmax &&
+                           (pa == PA_UPDATE || (pa == PA_XONLY && st->mode == MODE_DONE && st->status == GSE_MAXITER));
+    double xacc = 0.0;
     double* __restrict__ x = S.x;
     double* __restrict__ p = S.p;
     double* __restrict__ r = S.r;
@@ -640,8 +630,16 @@ __global__ void __launch_bounds__(256) k_cg_p3(const SysDesc* __restrict__ sys, 
             int64_t i = i0;
             for (; i + di < n2; i += 2 * di) {
                 const double2 pa2 = p2[i], xa = x2[i], pb = p2[i + di], xb = x2[i + di];
-                x2[i] = make_double2(fma(alpha, pa2.x, xa.x), fma(alpha, pa2.y, xa.y));
-                x2[i + di] = make_double2(fma(alpha, pb.x, xb.x), fma(alpha, pb.y, xb.y));
+                const double2 na = make_double2(fma(alpha, pa2.x, xa.x), fma(alpha, pa2.y, xa.y));
+                const double2 nb = make_double2(fma(alpha, pb.x, xb.x), fma(alpha, pb.y, xb.y));
+                x2[i] = na;
+                x2[i + di] = nb;
+                if (floor_due) {
+                    xacc = fma(na.x, na.x, xacc);
+                    xacc = fma(na.y, na.y, xacc);
+                    xacc = fma(nb.x, nb.x, xacc);
+                    xacc = fma(nb.y, nb.y, xacc);
+                }
                 if (upd) {
                     const double2 ra = r2[i], rb = r2[i + di];
                     p2[i] = make_double2(fma(beta, pa2.x, ra.x), fma(beta, pa2.y, ra.y));
@@ -650,7 +648,12 @@ __global__ void __launch_bounds__(256) k_cg_p3(const SysDesc* __restrict__ sys, 
             }
             if (i < n2) {
                 const double2 pa2 = p2[i], xa = x2[i];
-                x2[i] = make_double2(fma(alpha, pa2.x, xa.x), fma(alpha, pa2.y, xa.y));
+                const double2 na = make_double2(fma(alpha, pa2.x, xa.x), fma(alpha, pa2.y, xa.y));
+                x2[i] = na;
+                if (floor_due) {
+                    xacc = fma(na.x, na.x, xacc);
+                    xacc = fma(na.y, na.y, xacc);
+                }
                 if (upd) {
                     const double2 ra = r2[i];
                     p2[i] = make_double2(fma(beta, pa2.x, ra.x), fma(beta, pa2.y, ra.y));
@@ -661,7 +664,9 @@ __global__ void __launch_bounds__(256) k_cg_p3(const SysDesc* __restrict__ sys, 
         // the scalar loop: every element, or (pairs above) an odd last one
         for (int64_t i = S.vec2 ? (i0 == 0 ? j0 : n) : i0; i < n; i += di) {
             const double pi = p[i];
-            x[i] = fma(alpha, pi, x[i]);
+            const double xi = fma(alpha, pi, x[i]);
+            x[i] = xi;
+            if (floor_due) xacc = fma(xi, xi, xacc);
             if (upd) p[i] = fma(beta, pi, r[i]);
         }
     } else if (pa == PA_COPY_R) {
@@ -674,6 +679,19 @@ __global__ void __launch_bounds__(256) k_cg_p3(const SysDesc* __restrict__ sys, 
         }
     } else {
         for (int64_t i = i0; i < n; i += di) x[i] = 0.0;
+    }
+    if (floor_due) {
+        __shared__ double red[32];
+        double total_x;
+        if (!sys_grid_sum(xacc, S.partial, S.counter + 2, lb, nblk, red, &total_x)) return;
+        if (threadIdx.x == 0) {
+            st->p_action = PA_NONE;
+            if (total_x > 0.0 && st->res <= S.prm.eta[st->k] * sqrt(total_x) / st->nb) {
+                step_level(st);
+                if (st->mode != MODE_DONE) st->mode = MODE_RESID_R;   // at max_iter: the level only
+            }
+        }
+        return;
     }
     if (!sys_grid_last(S.counter + 2, nblk)) return;
     if (threadIdx.x == 0) st->p_action = PA_NONE;
