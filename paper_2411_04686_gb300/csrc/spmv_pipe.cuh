@@ -671,6 +671,28 @@ __device__ __forceinline__ double compute_chunk_direct(const MatView& m, const E
     double xv[8];
 #pragma unroll
     for (int i = 0; i < 8; i++) xv[i] = __ldg(x + col_of(m, col[i]));
+    if (__ballot_sync(FULL, bits != 0u) == 0u) {
+        // No row ends in the chunk: all 256 nonzeros belong to one row (begun
+        // here or earlier, going on past the chunk).  Each lane sums its 8 in
+        // two interleaved chains, the warp adds the lanes by a butterfly, and
+        // the chunk's piece goes to part / carry for the split-row pass.
+        double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+        for (int i = 0; i < 8; i += 2) {
+            s0 = fma(a[i], xv[i], s0);
+            s1 = fma(a[i + 1], xv[i + 1], s1);
+        }
+        double v = s0 + s1;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+        double dot = 0.0;
+        if (lane == 0 && sc.row0 < m.n_nonempty) {
+            if (DOT) dot = __ldg(e.p + actual_row(m, sc.row0)) * v;
+            if (sc.starts_mid) m.part[c] = v;
+            else m.carry[c] = v;
+        }
+        return dot;
+    }
     const int cnt = __popc(bits);
     int incl = cnt;
 #pragma unroll
