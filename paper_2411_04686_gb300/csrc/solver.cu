@@ -595,7 +595,70 @@ __global__ void __launch_bounds__(256) k_cg_p2(const SysDesc* __restrict__ sys, 
 
 // ---- P3: x and p updates --------------------------------------------------
 
-__global__ void __launch_bounds__(256) k_cg_p3(const SysDesc* __restrict__ sys, const int2* __restrict__ map) {
+// x += alpha p (and p = r + beta p when upd) over the block's share, element
+// pairs when the vectors allow it; with FLOOR, returns the block's share of
+// ||x_j||^2 of the x it stores.
+template <bool FLOOR>
+__device__ __forceinline__ double p3_update(const SysDesc& S, bool upd, double alpha, double beta, int64_t i0,
+                                            int64_t di) {
+    const int64_t n = S.n;
+    double* __restrict__ x = S.x;
+    double* __restrict__ p = S.p;
+    const double* __restrict__ r = S.r;
+    double xacc = 0.0;
+    int64_t j0 = 0;
+    if (S.vec2) {
+        // pairs of elements (16-byte loads), two pairs in flight per thread
+        const int64_t n2 = n >> 1;
+        double2* __restrict__ x2 = reinterpret_cast<double2*>(x);
+        double2* __restrict__ p2 = reinterpret_cast<double2*>(p);
+        const double2* __restrict__ r2 = reinterpret_cast<const double2*>(r);
+        int64_t i = i0;
+        for (; i + di < n2; i += 2 * di) {
+            const double2 pa2 = p2[i], xa = x2[i], pb = p2[i + di], xb = x2[i + di];
+            const double2 na = make_double2(fma(alpha, pa2.x, xa.x), fma(alpha, pa2.y, xa.y));
+            const double2 nb = make_double2(fma(alpha, pb.x, xb.x), fma(alpha, pb.y, xb.y));
+            x2[i] = na;
+            x2[i + di] = nb;
+            if constexpr (FLOOR) {
+                xacc = fma(na.x, na.x, xacc);
+                xacc = fma(na.y, na.y, xacc);
+                xacc = fma(nb.x, nb.x, xacc);
+                xacc = fma(nb.y, nb.y, xacc);
+            }
+            if (upd) {
+                const double2 ra = r2[i], rb = r2[i + di];
+                p2[i] = make_double2(fma(beta, pa2.x, ra.x), fma(beta, pa2.y, ra.y));
+                p2[i + di] = make_double2(fma(beta, pb.x, rb.x), fma(beta, pb.y, rb.y));
+            }
+        }
+        if (i < n2) {
+            const double2 pa2 = p2[i], xa = x2[i];
+            const double2 na = make_double2(fma(alpha, pa2.x, xa.x), fma(alpha, pa2.y, xa.y));
+            x2[i] = na;
+            if constexpr (FLOOR) {
+                xacc = fma(na.x, na.x, xacc);
+                xacc = fma(na.y, na.y, xacc);
+            }
+            if (upd) {
+                const double2 ra = r2[i];
+                p2[i] = make_double2(fma(beta, pa2.x, ra.x), fma(beta, pa2.y, ra.y));
+            }
+        }
+        j0 = 2 * n2;
+    }
+    // the scalar loop: every element, or (pairs above) an odd last one
+    for (int64_t i = S.vec2 ? (i0 == 0 ? j0 : n) : i0; i < n; i += di) {
+        const double pi = p[i];
+        const double xi = fma(alpha, pi, x[i]);
+        x[i] = xi;
+        if constexpr (FLOOR) xacc = fma(xi, xi, xacc);
+        if (upd) p[i] = fma(beta, pi, r[i]);
+    }
+    return xacc;
+}
+
+__global__ void __launch_bounds__(256, 5) k_cg_p3(const SysDesc* __restrict__ sys, const int2* __restrict__ map) {
     const int2 bm = map[blockIdx.x];
     const SysDesc& S = sys[bm.x];
     CgState* st = S.st;
@@ -604,6 +667,11 @@ __global__ void __launch_bounds__(256) k_cg_p3(const SysDesc* __restrict__ sys, 
     const int lb = bm.y, nblk = S.nblk_vec;
     const int64_t n = S.n;
     const double alpha = st->alpha, beta = st->beta;
+    double* __restrict__ x = S.x;
+    double* __restrict__ p = S.p;
+    double* __restrict__ r = S.r;
+    const double* __restrict__ q = S.q;
+    const int64_t i0 = (int64_t)lb * blockDim.x + threadIdx.x, di = (int64_t)nblk * blockDim.x;
     // The floor rule (GSE_POLICY_FLOOR, checked before the stagnation test in
     // the iteration's order) compares res_j with eta_k ||x_j|| / ||b||, x_j the
     // iterate this pass stores.  It is due when P2 let the iteration continue
@@ -612,75 +680,8 @@ __global__ void __launch_bounds__(256) k_cg_p3(const SysDesc* __restrict__ sys, 
     // over the system's blocks (all read the same state).
     const bool floor_due = (S.prm.flags & GSE_POLICY_FLOOR) && st->k < S.prm.kmax &&
                            (pa == PA_UPDATE || (pa == PA_XONLY && st->mode == MODE_DONE && st->status == GSE_MAXITER));
-    double xacc = 0.0;
-    double* __restrict__ x = S.x;
-    double* __restrict__ p = S.p;
-    double* __restrict__ r = S.r;
-    const double* __restrict__ q = S.q;
-    const int64_t i0 = (int64_t)lb * blockDim.x + threadIdx.x, di = (int64_t)nblk * blockDim.x;
-    if (pa == PA_UPDATE || pa == PA_XONLY) {
-        const bool upd = pa == PA_UPDATE;
-        int64_t j0 = 0;
-        if (S.vec2) {
-            // pairs of elements (16-byte loads), two pairs in flight per thread
-            const int64_t n2 = n >> 1;
-            double2* __restrict__ x2 = reinterpret_cast<double2*>(x);
-            double2* __restrict__ p2 = reinterpret_cast<double2*>(p);
-            const double2* __restrict__ r2 = reinterpret_cast<const double2*>(r);
-            int64_t i = i0;
-            for (; i + di < n2; i += 2 * di) {
-                const double2 pa2 = p2[i], xa = x2[i], pb = p2[i + di], xb = x2[i + di];
-                const double2 na = make_double2(fma(alpha, pa2.x, xa.x), fma(alpha, pa2.y, xa.y));
-                const double2 nb = make_double2(fma(alpha, pb.x, xb.x), fma(alpha, pb.y, xb.y));
-                x2[i] = na;
-                x2[i + di] = nb;
-                if (floor_due) {
-                    xacc = fma(na.x, na.x, xacc);
-                    xacc = fma(na.y, na.y, xacc);
-                    xacc = fma(nb.x, nb.x, xacc);
-                    xacc = fma(nb.y, nb.y, xacc);
-                }
-                if (upd) {
-                    const double2 ra = r2[i], rb = r2[i + di];
-                    p2[i] = make_double2(fma(beta, pa2.x, ra.x), fma(beta, pa2.y, ra.y));
-                    p2[i + di] = make_double2(fma(beta, pb.x, rb.x), fma(beta, pb.y, rb.y));
-                }
-            }
-            if (i < n2) {
-                const double2 pa2 = p2[i], xa = x2[i];
-                const double2 na = make_double2(fma(alpha, pa2.x, xa.x), fma(alpha, pa2.y, xa.y));
-                x2[i] = na;
-                if (floor_due) {
-                    xacc = fma(na.x, na.x, xacc);
-                    xacc = fma(na.y, na.y, xacc);
-                }
-                if (upd) {
-                    const double2 ra = r2[i];
-                    p2[i] = make_double2(fma(beta, pa2.x, ra.x), fma(beta, pa2.y, ra.y));
-                }
-            }
-            j0 = 2 * n2;
-        }
-        // the scalar loop: every element, or (pairs above) an odd last one
-        for (int64_t i = S.vec2 ? (i0 == 0 ? j0 : n) : i0; i < n; i += di) {
-            const double pi = p[i];
-            const double xi = fma(alpha, pi, x[i]);
-            x[i] = xi;
-            if (floor_due) xacc = fma(xi, xi, xacc);
-            if (upd) p[i] = fma(beta, pi, r[i]);
-        }
-    } else if (pa == PA_COPY_R) {
-        for (int64_t i = i0; i < n; i += di) p[i] = r[i];
-    } else if (pa == PA_COPY_Q) {
-        for (int64_t i = i0; i < n; i += di) {
-            const double v = q[i];
-            r[i] = v;
-            p[i] = v;
-        }
-    } else {
-        for (int64_t i = i0; i < n; i += di) x[i] = 0.0;
-    }
     if (floor_due) {
+        const double xacc = p3_update<true>(S, pa == PA_UPDATE, alpha, beta, i0, di);
         __shared__ double red[32];
         double total_x;
         if (!sys_grid_sum(xacc, S.partial, S.counter + 2, lb, nblk, red, &total_x)) return;
@@ -692,6 +693,19 @@ __global__ void __launch_bounds__(256) k_cg_p3(const SysDesc* __restrict__ sys, 
             }
         }
         return;
+    }
+    if (pa == PA_UPDATE || pa == PA_XONLY) {
+        p3_update<false>(S, pa == PA_UPDATE, alpha, beta, i0, di);
+    } else if (pa == PA_COPY_R) {
+        for (int64_t i = i0; i < n; i += di) p[i] = r[i];
+    } else if (pa == PA_COPY_Q) {
+        for (int64_t i = i0; i < n; i += di) {
+            const double v = q[i];
+            r[i] = v;
+            p[i] = v;
+        }
+    } else {
+        for (int64_t i = i0; i < n; i += di) x[i] = 0.0;
     }
     if (!sys_grid_last(S.counter + 2, nblk)) return;
     if (threadIdx.x == 0) st->p_action = PA_NONE;

@@ -246,6 +246,61 @@ def test_stepped_cg_on_each_engine_schedule(sched):
     assert np.max(np.abs(x.cpu().numpy() - ref["x"])) < 1e-8
 
 
+def _arrow_spd(n=3000, dense=4, seed=3):
+    """Symmetric, strictly diagonally dominant (so SPD) matrix: a tridiagonal band
+    plus `dense` full rows and columns, values not dyadic.  Its dense rows span
+    whole 256-nonzero chunks with no row end."""
+    rng = np.random.default_rng(seed)
+    rows, cols, vals = [], [], []
+    for i in range(n - 1):
+        v = -1.0 / 3.0 - 0.1 * rng.random()
+        rows += [i, i + 1]; cols += [i + 1, i]; vals += [v, v]
+    for k in range(dense):
+        w = (rng.random(n) - 0.5) * 0.02 / 3.0
+        for j in range(dense, n):
+            rows += [k, j]; cols += [j, k]; vals += [w[j], w[j]]
+    off = {}
+    for r, c, v in zip(rows, cols, vals):
+        off[(r, c)] = off.get((r, c), 0.0) + v
+    rsum = np.zeros(n)
+    for (r, c), v in off.items():
+        rsum[r] += abs(v)
+    for i in range(n):
+        off[(i, i)] = rsum[i] + 0.05 + 0.01 * rng.random()
+    keys = sorted(off)
+    r = np.array([k[0] for k in keys], dtype=np.int64)
+    row_ptr = np.zeros(n + 1, dtype=np.int32)
+    np.add.at(row_ptr, r + 1, 1)
+    row_ptr = np.cumsum(row_ptr).astype(np.int32)
+    col = np.array([k[1] for k in keys], dtype=np.int32)
+    val = np.array([off[k] for k in keys])
+    return synth.CSR(row_ptr, col, val, n, "arrow")
+
+
+def test_stepped_cg_nonzero_split_with_dense_rows():
+    """Rows longer than a chunk (chunks with no row end) through the engine's
+    nonzero-split SpMV phase with its p.Ap epilogue, against the oracle."""
+    A = _arrow_spd()
+    assert np.diff(A.row_ptr).max() > 2 * 256
+    M = gse.GseMatrix.from_csr(A)
+    M.set_schedule(1)
+    b = synth.rhs_ones(A)
+    x = torch.zeros(A.n_rows, dtype=torch.float64, device="cuda")
+    info = M.cg(_dev(b), x, tol=1e-10, policy=gse.SCALED_CG)
+    ref = oracle.stepped_cg(A.row_ptr, A.col, oracle.levels(A.val), b, tol=1e-10, policy=oracle.SCALED_CG)
+    assert info["status"] == gse.OK and info["rel_res_true"] < 1e-10
+    assert info["k_final"] == ref["info"]["k_final"]
+    assert abs(info["iters"] - ref["info"]["iters"]) <= 3
+    assert np.max(np.abs(x.cpu().numpy() - ref["x"])) < 1e-8
+    # the standalone SpMV on the same matrix at every level, row by row
+    xv = synth.uniform_x(A.n_cols, seed=5)
+    enc = oracle.encode(A.val)
+    for k in (1, 2, 3):
+        y = M.spmv(k, _dev(xv)).cpu().numpy()
+        yref, yabs = oracle.spmv_dot2(A.row_ptr, A.col, oracle.decode(*enc, k), xv)
+        assert np.all(np.abs(y - yref) <= 1e-13 * yabs), k
+
+
 def test_server_mixed_stream_equals_solo():
     """Served solves (continuous batching, admission by a memory budget that
     lets only a few systems in at once) give the solo results bit for bit."""
