@@ -897,7 +897,8 @@ def served_benchmark(gse, torch, nreq, rate, rank, world, rate_factors=(0.5,)):
     distribution (a pool of 64 systems), admitted by HBM footprint into a
     continuous batch; p50/p99 latency from arrival to completion.  One run per
     arrival rate factor (times the saturated batch throughput `rate`); the
-    first factor's run is reported at the top level, all of them in `sweep`."""
+    first factor's run is reported at the top level, all of them in `sweep`,
+    and the 1x stream once more under SCALED_CG + the floor rule."""
     from paper_2411_04686_gb300 import serve
     specs = synth.batch_specs(64, seed=1)
     pool = []
@@ -910,6 +911,10 @@ def served_benchmark(gse, torch, nreq, rate, rank, world, rate_factors=(0.5,)):
         sweep[-1]["rate_factor"] = f
     out = dict(sweep[0])
     out["sweep"] = sweep
+    # the same arrival stream at 1x under SCALED_CG + the floor rule, which does
+    # less work per system (row-iterations 1.13x FP64's instead of 1.69x)
+    floor = gse.Policy(**{**gse.SCALED_CG.__dict__, "flags": gse.POLICY_FLOOR})
+    out["floor_policy_1x"] = _served_run(gse, serve, pool, nreq, rate, rank, world, policy=floor)
     # one-at-a-time FP64 CSR CG throughput on the same pool (8 systems)
     t_single = 0.0
     for A, b in pool[:8]:
@@ -926,7 +931,7 @@ def served_benchmark(gse, torch, nreq, rate, rank, world, rate_factors=(0.5,)):
     return out
 
 
-def _served_run(gse, serve, pool, nreq, rate, rank, world):
+def _served_run(gse, serve, pool, nreq, rate, rank, world, policy=None):
     arrivals = serve.poisson_arrivals(nreq, rate, seed=2)
     rng = np.random.default_rng(3)
     picks = rng.integers(0, len(pool), nreq)
@@ -934,7 +939,7 @@ def _served_run(gse, serve, pool, nreq, rate, rank, world):
             for i in range(nreq)]
     if world > 1:
         reqs = serve.shard(reqs, rank, world)
-    srv = serve.Server(lambda i: pool[i], capacity=64, slots_per_step=16, backlog_slots_per_step=32)
+    srv = serve.Server(lambda i: pool[i], capacity=64, slots_per_step=16, backlog_slots_per_step=32, policy=policy)
     t0 = time.perf_counter()
     srv.clock = lambda: time.perf_counter() - t0
     k = 0
