@@ -39,6 +39,21 @@ __global__ void __launch_bounds__(256) k_spmv_direct(MatView m, const double* __
     spmv_chunks_direct<K, R, false, RESID>(m, x, e, gw, ((int64_t)gridDim.x * blockDim.x) >> 5, n_chunks);
 }
 
+// The same at level 3 for a handle in the default layout (groups of 32,
+// segments 16/16/20, no table): the decoder's widths are compile-time
+// constants, and at 64 registers an SM holds 4 CTAs (the general level-3
+// kernel: 3).  The values are the same bits.
+template <bool RESID>
+__global__ void __launch_bounds__(256, 4) k_spmv_direct_std3(MatView m, const double* __restrict__ x, Epi e,
+                                                             int64_t n_chunks, ChunkStage L, int* err, const int* gate) {
+    if (gate && *gate) return;
+    (void)L;
+    (void)err;
+    fill_empty_rows(m, e, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    spmv_chunks_direct<3, 4, false, RESID, true>(m, x, e, gw, ((int64_t)gridDim.x * blockDim.x) >> 5, n_chunks);
+}
+
 // Finishes the rows that cross chunk boundaries (after k_spmv, same stream).
 template <int UPL>
 __global__ void __launch_bounds__(256) k_spmv_fix(MatView m, Epi e, int64_t n_chunks, const int* gate) {
@@ -307,6 +322,17 @@ static KernelPick pick_kernel_t(int k, int r_lo, int upl) {
     }
 }
 
+// The level-3 direct nonzero split for a handle in the default layout.
+template <bool RESID>
+static KernelPick pick_direct_std3() {
+    KernelPick kp;
+    kp.fn = k_spmv_direct_std3<RESID>;
+    kp.warps = 8;
+    kp.L = chunk_stage_layout<3, 4, 1>(8, 4);    // unused by the kernel
+    kp.smem = 0;
+    return kp;
+}
+
 static KernelPick pick_kernel(int k, int r_lo, int upl, bool resid, bool tbl) {
     if (tbl) return resid ? pick_kernel_tbl<true>(k, r_lo) : pick_kernel_tbl<false>(k, r_lo);
     return resid ? pick_kernel_t<true>(k, r_lo, upl) : pick_kernel_t<false>(k, r_lo, upl);
@@ -322,7 +348,10 @@ int launch_spmv(gse_matrix* h, int k, int epi, const SpmvArgs& a, cudaStream_t s
     int upl = upl_override ? upl_override : units_per_lane(h);
     if (upl == GSE_SCHEDULE_ROWS) return lanerow_ok(h, k) ? launch_lanerow(h, k, epi, a, s) : launch_rows(h, k, epi, a, s);
     if (h->v.tbl || src16(k)) upl = 1;         // the table format and the 16-bit baselines run one unit per lane
-    const KernelPick kp = pick_kernel(k, h->v.r_lo, upl, epi == EPI_RESID, h->v.tbl != 0);
+    const bool std3 = upl == 1 && k == 3 && h->n_seg == 3 && lanerow_format(h->v, h->group_size, h->n_seg) &&
+                      h->v.col_mask == 0xFFFFFFFFu;
+    const KernelPick kp = std3 ? (epi == EPI_RESID ? pick_direct_std3<true>() : pick_direct_std3<false>())
+                               : pick_kernel(k, h->v.r_lo, upl, epi == EPI_RESID, h->v.tbl != 0);
     const int64_t ch = 256 * upl;
     const int64_t n_chunks = (h->v.nnz + ch - 1) / ch;
     const int64_t resident = (int64_t)h->num_sms * resident_blocks(kp);

@@ -26,6 +26,23 @@ enum { SRC_FP16 = 16, SRC_BF16 = 17, SRC_FP32 = 32, SRC_FP64 = 64 };
 // 16-bit value sources (the baselines stored in 2 bytes per nonzero).
 __host__ __device__ constexpr bool src16(int K) { return K == SRC_FP16 || K == SRC_BF16; }
 
+// The default layout (segments 16/16/20, groups of 32, no exponent table) with
+// its widths as compile-time constants: the decoders read the same fields from
+// it as from a MatView, so a kernel built on it decodes bit-identically with
+// the shifts folded.
+struct StdLayout {
+    static constexpr int W1 = 15, s2 = 16, s3 = 20, W2 = 31, W3 = 51;
+};
+// The widths a decoder reads: the view's own (run time) or the default layout's.
+template <bool STD>
+struct WidthsOf {
+    static __device__ __forceinline__ const MatView& get(const MatView& m) { return m; }
+};
+template <>
+struct WidthsOf<true> {
+    static __device__ __forceinline__ StdLayout get(const MatView&) { return StdLayout{}; }
+};
+
 // ---- decode (Alg. 2 and the concatenated tails) --------------------------------
 
 // Subnormal results only: ldexp-style rounding (exact first scaling, one rounding).
@@ -36,7 +53,8 @@ static __device__ __noinline__ double decode_tiny(uint64_t M, int Eg, int Wk, ui
 }
 
 // Level 1: M_1 = head magnitude (W_1 <= 15 bits).
-__device__ __forceinline__ double decode_l1(uint32_t h, int Eg, const MatView& m) {
+template <class V>
+__device__ __forceinline__ double decode_l1(uint32_t h, int Eg, const V& m) {
     const uint32_t mag = h & ((1u << m.W1) - 1u);
     const uint32_t sign = (h >> m.W1) & 1u;
     const int lz = __clz(mag);                       // leading one at bit 31 - lz
@@ -50,7 +68,8 @@ __device__ __forceinline__ double decode_l1(uint32_t h, int Eg, const MatView& m
 // from the FP32 image of M_1 (exact: M_1 < 2^24, built by integer insertion and
 // one FP32 subtraction), so the FP64 high word is that image shifted right by 3
 // plus an exponent offset.  eoff = (E_g - W_1 - 127) << 20, per group.
-__device__ __forceinline__ double decode_l1_f(uint32_t h, int Eg, uint32_t eoff, const MatView& m) {
+template <class V>
+__device__ __forceinline__ double decode_l1_f(uint32_t h, int Eg, uint32_t eoff, const V& m) {
     const uint32_t mag = h & ((1u << m.W1) - 1u);
     const uint32_t sign = (h >> m.W1) << 31;
     const float f = __uint_as_float(0x4B000000u | mag) - 8388608.0f;   // == (float)mag
@@ -61,7 +80,8 @@ __device__ __forceinline__ double decode_l1_f(uint32_t h, int Eg, uint32_t eoff,
 }
 
 // Level 2: M_2 = head magnitude << s2 | tail1 (W_2 <= 31 bits).
-__device__ __forceinline__ double decode_l2(uint32_t h, uint32_t t1, int Eg, const MatView& m) {
+template <class V>
+__device__ __forceinline__ double decode_l2(uint32_t h, uint32_t t1, int Eg, const V& m) {
     const uint32_t M = ((h & ((1u << m.W1) - 1u)) << m.s2) | t1;
     const uint32_t sign = (h >> m.W1) & 1u;
     const int lz = __clz(M);
@@ -73,8 +93,9 @@ __device__ __forceinline__ double decode_l2(uint32_t h, uint32_t t1, int Eg, con
 }
 
 // Level 3: M_3 = M_2 << s3 | tail2 (W_3 <= 63 bits).
+template <class V>
 __device__ __forceinline__ double decode_l3(uint32_t h, uint32_t t1, uint32_t t2, int Eg,
-                                            const MatView& m) {
+                                            const V& m) {
     const uint64_t M = ((uint64_t)((((h & ((1u << m.W1) - 1u)) << m.s2) | t1)) << m.s3) | t2;
     const uint32_t sign = (h >> m.W1) & 1u;
     const int lz = __clzll(M);
@@ -114,7 +135,8 @@ __device__ __forceinline__ double decode_l3_fast(uint32_t h, uint32_t t1, uint32
 // segments after it are shifted in right below.  Bit-identical to decode_l3
 // for every value (zero and, via the group test Eg <= W_3, subnormal results
 // included).
-__device__ __forceinline__ double decode_l3_sel(uint32_t h, uint32_t t1, uint32_t t2, int Eg, const MatView& m) {
+template <class V>
+__device__ __forceinline__ double decode_l3_sel(uint32_t h, uint32_t t1, uint32_t t2, int Eg, const V& m) {
     const uint32_t mag = h & ((1u << m.W1) - 1u);
     if (Eg <= m.W3) return decode_l3(h, t1, t2, Eg, m);          // results may be subnormal: exact path
     const bool in_h = mag != 0, in_1 = t1 != 0;
@@ -177,7 +199,7 @@ __device__ __forceinline__ uint32_t u16_of(const uint4& w, int i) {
 
 // Loads unit u and rebuilds its 8 values.  R: bits of tail2 kept in the packed
 // low array (0, 4, 8 or 16; -1 reads the width from the view at run time).
-template <int K, int R>
+template <int K, int R, bool STD = false>
 __device__ __forceinline__ void load_unit(const MatView& m, int64_t u, int* col, double* a) {
     const int4* c4 = reinterpret_cast<const int4*>(m.col) + 2 * u;
     const int4 ca = __ldg(c4), cb = __ldg(c4 + 1);
@@ -201,7 +223,9 @@ __device__ __forceinline__ void load_unit(const MatView& m, int64_t u, int* col,
 #pragma unroll
         for (int i = 0; i < 8; i++) a[i] = widen16<K>(u16_of(w, i));
     } else {
-        const int Eg0 = m.tbl ? 0 : (int)__ldg(m.gexp + ((u * GSE_UNIT) >> m.g_shift));
+        // STD: the default layout (checked at launch): groups of 32, no table
+        const bool tbl = !STD && m.tbl;
+        const int Eg0 = tbl ? 0 : (int)__ldg(m.gexp + ((u * GSE_UNIT) >> (STD ? 5 : m.g_shift)));
         const uint4 hw = __ldcs(reinterpret_cast<const uint4*>(m.head) + u);
         uint4 t1w = make_uint4(0, 0, 0, 0), t2w = make_uint4(0, 0, 0, 0);
         uint32_t lo[4] = {0, 0, 0, 0};
@@ -217,14 +241,15 @@ __device__ __forceinline__ void load_unit(const MatView& m, int64_t u, int* col,
                 else if (m.r_lo == 16) { const uint4 l4 = __ldcs(reinterpret_cast<const uint4*>(m.t2lo) + u); lo[0] = l4.x; lo[1] = l4.y; lo[2] = l4.z; lo[3] = l4.w; }
             }
         }
+        const auto& L = WidthsOf<STD>::get(m);
 #pragma unroll
         for (int i = 0; i < 8; i++) {
             uint32_t h = u16_of(hw, i);
-            const int Eg = m.tbl ? (int)__ldg(m.etab + tbl_index(m, col[i], h)) : Eg0;   // table format: per value
+            const int Eg = tbl ? (int)__ldg(m.etab + tbl_index(m, col[i], h)) : Eg0;   // table format: per value
             if constexpr (K == 1) {
-                a[i] = decode_l1_f(h, Eg, (uint32_t)(Eg - m.W1 - 127) << 20, m);
+                a[i] = decode_l1_f(h, Eg, (uint32_t)(Eg - L.W1 - 127) << 20, L);
             } else if constexpr (K == 2) {
-                a[i] = decode_l2(h, u16_of(t1w, i), Eg, m);
+                a[i] = decode_l2(h, u16_of(t1w, i), Eg, L);
             } else {
                 uint32_t t2 = u16_of(t2w, i);
                 if constexpr (R > 0) {
@@ -236,8 +261,8 @@ __device__ __forceinline__ void load_unit(const MatView& m, int64_t u, int* col,
                         t2 = (t2 << m.r_lo) | ((lo[bit >> 5] >> (bit & 31)) & ((1u << m.r_lo) - 1u));
                     }
                 }
-                if constexpr (R == 0 || R == 4) a[i] = decode_l3_sel(h, u16_of(t1w, i), t2, Eg, m);
-                else a[i] = decode_l3(h, u16_of(t1w, i), t2, Eg, m);
+                if constexpr (R == 0 || R == 4) a[i] = decode_l3_sel(h, u16_of(t1w, i), t2, Eg, L);
+                else a[i] = decode_l3(h, u16_of(t1w, i), t2, Eg, L);
             }
         }
     }

@@ -658,7 +658,7 @@ __device__ __forceinline__ double spmv_chunks_block(const MatView& m, const doub
 // stage ring every SM keeps its whole L1 for the random x gathers, which is
 // what matrices with scattered columns are bound by; this is the default
 // nonzero-split kernel (the staged ring above serves 2 and 4 units per lane).
-template <int K, int R, bool DOT, bool RESID>
+template <int K, int R, bool DOT, bool RESID, bool STD = false>
 __device__ __forceinline__ double compute_chunk_direct(const MatView& m, const Epi& e, int64_t c,
                                                        const double* __restrict__ x) {
     const unsigned FULL = 0xFFFFFFFFu;
@@ -667,7 +667,7 @@ __device__ __forceinline__ double compute_chunk_direct(const MatView& m, const E
     const uint32_t bits = (__ldg(m.rowend + ((c * 256) >> 5) + (lane >> 2)) >> ((lane & 3) * 8)) & 0xFFu;
     int col[8];
     double a[8];
-    load_unit<K, R>(m, c * 32 + lane, col, a);
+    load_unit<K, R, STD>(m, c * 32 + lane, col, a);
     double xv[8];
 #pragma unroll
     for (int i = 0; i < 8; i++) xv[i] = __ldg(x + col_of(m, col[i]));
@@ -767,11 +767,13 @@ __device__ __forceinline__ double compute_chunk_direct(const MatView& m, const E
 }
 
 // Warps w0, w0 + wstride, ... of a launch take chunks w0, w0 + wstride, ...
-template <int K, int R, bool DOT, bool RESID>
+// STD: the handle has the default layout (StdLayout), decoded with its widths
+// as constants.
+template <int K, int R, bool DOT, bool RESID, bool STD = false>
 __device__ __forceinline__ double spmv_chunks_direct(const MatView& m, const double* __restrict__ x, const Epi& e,
                                                      int64_t w0, int64_t wstride, int64_t n_chunks) {
     double dot = 0.0;
-    for (int64_t c = w0; c < n_chunks; c += wstride) dot += compute_chunk_direct<K, R, DOT, RESID>(m, e, c, x);
+    for (int64_t c = w0; c < n_chunks; c += wstride) dot += compute_chunk_direct<K, R, DOT, RESID, STD>(m, e, c, x);
     return dot;
 }
 
