@@ -175,13 +175,16 @@ __device__ __forceinline__ double lr_fast(uint32_t h, uint32_t t1, uint32_t t2, 
     return __hiloint2double((int)hi, (int)lo);
 }
 
-// General decode of one value with its own group exponent (any head).
+// General decode of one value with its own group exponent (any head).  A
+// handle on this kernel has the default layout (lanerow_format), so the
+// decoders take its widths as compile-time constants.
 template <int K>
 __device__ __forceinline__ double lr_general(const MatView& m, uint32_t h, uint32_t t1, uint32_t t2, uint32_t nib,
                                              int Eg) {
-    if constexpr (K == 1) return decode_l1(h, Eg, m);
-    else if constexpr (K == 2) return decode_l2(h, t1, Eg, m);
-    else return decode_l3(h, t1, (t2 << 4) | nib, Eg, m);
+    (void)m;
+    if constexpr (K == 1) return decode_l1(h, Eg, StdLayout{});
+    else if constexpr (K == 2) return decode_l2(h, t1, Eg, StdLayout{});
+    else return decode_l3(h, t1, (t2 << 4) | nib, Eg, StdLayout{});
 }
 
 // The rows of one lane within a staged tile (R of them: rows l, 32 + l, ...).
