@@ -120,6 +120,29 @@ def test_spmv_levels_against_oracle(name, upl):
     M.free()
 
 
+@pytest.mark.parametrize("seg,G", [((16, 16, 32), 32), ((16, 16, 16), 32), ((12, 16, 24), 32), ((16, 8, 8), 32),
+                                   ((2, 16, 20), 32), ((16, 16, 20), 16), ((16, 16), 32), ((16,), 32)])
+@pytest.mark.parametrize("upl", [1, 2, gse.SCHEDULE_ROWS])
+def test_spmv_other_layouts_against_oracle(seg, G, upl):
+    """Segment widths and group sizes other than the default 16/16/20 with groups
+    of 32: the kernels read the widths from the matrix view (the default layout
+    runs kernels with the widths compiled in)."""
+    for A in (synth.powerlaw_random(20000, 16.0, 2048, seed=21), synth.poisson2d(40, 1.0 / 3.0)):
+        M = gse.GseMatrix.from_csr(A, group_size=G, seg_bits=seg)
+        try:
+            M.set_schedule(upl)
+        except gse.GseError as e:        # a row block too wide for the row schedule
+            assert upl == gse.SCHEDULE_ROWS and e.code == gse.ERR_UNSUPPORTED
+            M.free()
+            continue
+        x = synth.uniform_x(A.n_cols, seed=6)
+        xd = torch.from_numpy(x).cuda()
+        enc = oracle.encode(A.val, G, seg)
+        for k in range(1, len(seg) + 1):
+            check_spmv_rows(M.spmv(k, xd).cpu().numpy(), A, oracle.decode(*enc, k, G, seg), x)
+        M.free()
+
+
 def test_x_ones_integer_matrix_exact():
     """Sec. IV-A's x = 1 setting: 5-point Poisson at every level is exact."""
     A = synth.poisson2d(64)
