@@ -93,6 +93,35 @@ def test_batch_cg_against_oracle(mix):
         M.free()
 
 
+def test_batch_cg_floor_policy_against_oracle(mix):
+    """The batch under the scaled policy plus the perturbation-floor trigger
+    (reading R20; its decision is taken per system in the x-update phase)
+    steps at the oracle's iterations, system by system, and equals each
+    system's solo solve bit for bit."""
+    pol = gse.Policy(**{**gse.SCALED_CG.__dict__, "flags": gse.POLICY_FLOOR})
+    opol = oracle.Policy(**{**oracle.SCALED_CG.__dict__, "flags": oracle.POLICY_FLOOR})
+    mats = [gse.GseMatrix.from_csr(A) for _, A, _, _, _ in mix]
+    bs = [_dev(b) for _, _, b, _, _ in mix]
+    xs = [torch.zeros(A.n_rows, dtype=torch.float64, device="cuda") for _, A, _, _, _ in mix]
+    rc, infos = gse.batch_cg(mats, bs, xs, policy=pol)
+    assert rc == gse.OK
+    for (spec, A, b, _, bound), M, x, info in zip(mix, mats, xs, infos):
+        ref = oracle.stepped_cg(A.row_ptr, A.col, oracle.levels(A.val), b, tol=1e-10, policy=opol)
+        ri = ref["info"]
+        assert info["status"] == gse.OK and ri["status"] == oracle.OK, (spec, info, ri)
+        assert info["k_final"] == ri["k_final"] == 3, (spec, info, ri)
+        assert info["switch_iter"] == ri["switch_iter"], (spec, info, ri)
+        assert abs(info["iters"] - ri["iters"]) <= 2, (spec, info, ri)
+        assert info["rel_res_true"] < 1e-10 and ri["rel_res_true"] < 1e-10
+        assert float(np.max(np.abs(x.cpu().numpy() - ref["x"]))) <= bound
+        x1 = torch.zeros(A.n_rows, dtype=torch.float64, device="cuda")
+        i1 = M.cg(_dev(b), x1, policy=pol)
+        assert info["iters"] == i1["iters"] and info["switch_iter"] == i1["switch_iter"]
+        assert torch.equal(x, x1)
+    for M in mats:
+        M.free()
+
+
 def test_engine_staggered_against_oracle(mix):
     """Systems join the engine while others are mid-solve (capacity 3, few
     slots per step) and each finishes where the oracle does."""
