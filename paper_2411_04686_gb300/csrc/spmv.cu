@@ -81,7 +81,9 @@ __global__ void __launch_bounds__(ROWS_WARPS * 32) k_spmv_rows(MatView m, const 
 // tiles round-robin.
 constexpr int LR_WARPS = 8;
 
-template <int K, bool RESID>
+// TBL: 0 the per-group format; 1 the global table (index in the column word),
+// general decode; 2 the same when every entry exceeds W_1 (fast decode).
+template <int K, bool RESID, int TBL = 0>
 __global__ void __launch_bounds__(LR_WARPS * 32) k_spmv_lanerow(MatView m, const double* __restrict__ x, Epi e,
                                                                  const int* gate) {
     if (gate && *gate) return;
@@ -89,29 +91,30 @@ __global__ void __launch_bounds__(LR_WARPS * 32) k_spmv_lanerow(MatView m, const
     constexpr int R = lr_rows_per_lane<K>();
     const int warp = threadIdx.x >> 5;
     const int64_t ntile = (m.n_rows + 32 * R - 1) / (32 * R);
-    lr_loop<K, false, RESID>(m, x, e, (int64_t)blockIdx.x * LR_WARPS + warp, (int64_t)gridDim.x * LR_WARPS, ntile,
-                             smem + warp * LR_STAGES * LrLayout<K, R>::BYTES);
+    lr_loop<K, false, RESID, R, TBL>(m, x, e, (int64_t)blockIdx.x * LR_WARPS + warp, (int64_t)gridDim.x * LR_WARPS,
+                                     ntile, smem + warp * LR_STAGES * LrLayout<K, R>::BYTES);
 }
 
 typedef void (*LaneRowKernel)(MatView, const double*, Epi, const int*);
 
 template <int K, bool RESID>
-static LaneRowKernel pick_lr(int* smem, int* rows) {
+static LaneRowKernel pick_lr(int* smem, int* rows, int tbl) {
     *smem = lr_smem<K>(LR_WARPS);
     *rows = lr_rows_per_lane<K>();
-    return k_spmv_lanerow<K, RESID>;
+    if (K > 3) return tbl ? k_spmv_lanerow<K, RESID, 1> : k_spmv_lanerow<K, RESID>;   // baselines: masked columns
+    return tbl == 2 ? k_spmv_lanerow<K, RESID, 2> : tbl == 1 ? k_spmv_lanerow<K, RESID, 1> : k_spmv_lanerow<K, RESID>;
 }
 
 template <bool RESID>
-static LaneRowKernel pick_lanerow_t(int k, int* smem, int* rows) {
+static LaneRowKernel pick_lanerow_t(int k, int* smem, int* rows, int tbl) {
     switch (k) {
-        case 1: return pick_lr<1, RESID>(smem, rows);
-        case 2: return pick_lr<2, RESID>(smem, rows);
-        case 3: return pick_lr<3, RESID>(smem, rows);
-        case SRC_FP32: return pick_lr<SRC_FP32, RESID>(smem, rows);
-        case SRC_FP16: return pick_lr<SRC_FP16, RESID>(smem, rows);
-        case SRC_BF16: return pick_lr<SRC_BF16, RESID>(smem, rows);
-        default: return pick_lr<SRC_FP64, RESID>(smem, rows);
+        case 1: return pick_lr<1, RESID>(smem, rows, tbl);
+        case 2: return pick_lr<2, RESID>(smem, rows, tbl);
+        case 3: return pick_lr<3, RESID>(smem, rows, tbl);
+        case SRC_FP32: return pick_lr<SRC_FP32, RESID>(smem, rows, tbl);
+        case SRC_FP16: return pick_lr<SRC_FP16, RESID>(smem, rows, tbl);
+        case SRC_BF16: return pick_lr<SRC_BF16, RESID>(smem, rows, tbl);
+        default: return pick_lr<SRC_FP64, RESID>(smem, rows, tbl);
     }
 }
 
@@ -209,20 +212,40 @@ static int launch_rows(gse_matrix* h, int k, int epi, const SpmvArgs& a, cudaStr
 // (32-row tiles within 256 nonzeros, 64-row tiles within 512), its rows are at
 // most 64 long, and its level decodes with the lane-row decoders (or is a
 // plain CSR baseline).
+static bool lanerow_spans_ok(const gse_matrix* h) {
+    return h->tile_span32 <= lr_cap_rows(1) && h->tile_span64 <= lr_cap_rows(2) && h->max_row_len <= 64 &&
+           h->v.n_rows < (int64_t)1 << 30;
+}
+
 bool lanerow_ok(const gse_matrix* h, int k) {
-    // the table format keeps exponent indices in the column words, which the
-    // lane-row kernel reads as plain columns: that format stays on the other
-    // kernels at every level, its baselines included
+    // the table format keeps exponent indices in the column words: the CG
+    // engine's lane-row phase reads them as plain columns, so that format
+    // stays on the engine's other kernels (the standalone SpMV below takes it)
     if (h->v.tbl || h->v.col_mask != 0xFFFFFFFFu) return false;
-    if (h->tile_span32 > lr_cap_rows(1) || h->tile_span64 > lr_cap_rows(2) || h->max_row_len > 64 ||
-        h->v.n_rows >= (int64_t)1 << 30)
-        return false;
+    if (!lanerow_spans_ok(h)) return false;
     return k > 3 || lanerow_format(h->v, h->group_size, h->n_seg);
+}
+
+// The standalone SpMV's lane-row test: lanerow_ok, or the table format with
+// its index in the column word (masked columns, per-value table exponents).
+static bool lanerow_ok_spmv(const gse_matrix* h, int k) {
+    return lanerow_ok(h, k) || (lanerow_format_tbl(h->v, h->n_seg) && lanerow_spans_ok(h));
+}
+
+// 0: per-group format; 1: table, general decode; 2: table, every entry above
+// W_1 so a nonzero head holds the leading one (fast decode).
+static int lanerow_table_kind(const gse_matrix* h) {
+    if (!h->v.tbl) return 0;
+    for (int i = 0; i < h->num_exp; i++)
+        if (h->etab_host[i] <= LR_W1) return 1;
+    return 2;
 }
 
 static int launch_lanerow(gse_matrix* h, int k, int epi, const SpmvArgs& a, cudaStream_t s) {
     int smem = 0, R = 1;
-    LaneRowKernel fn = epi == EPI_RESID ? pick_lanerow_t<true>(k, &smem, &R) : pick_lanerow_t<false>(k, &smem, &R);
+    const int tbl = lanerow_table_kind(h);
+    LaneRowKernel fn = epi == EPI_RESID ? pick_lanerow_t<true>(k, &smem, &R, tbl)
+                                        : pick_lanerow_t<false>(k, &smem, &R, tbl);
     int nb = occupancy_cached((const void*)fn, LR_WARPS * 32, (size_t)smem);
     if (nb < 1) nb = 1;
     const int64_t ntile = (h->v.n_rows + 32 * R - 1) / (32 * R);
@@ -346,7 +369,8 @@ static int resident_blocks(const KernelPick& kp) {
 
 int launch_spmv(gse_matrix* h, int k, int epi, const SpmvArgs& a, cudaStream_t s, int upl_override) {
     int upl = upl_override ? upl_override : units_per_lane(h);
-    if (upl == GSE_SCHEDULE_ROWS) return lanerow_ok(h, k) ? launch_lanerow(h, k, epi, a, s) : launch_rows(h, k, epi, a, s);
+    if (upl == GSE_SCHEDULE_ROWS)
+        return lanerow_ok_spmv(h, k) ? launch_lanerow(h, k, epi, a, s) : launch_rows(h, k, epi, a, s);
     if (h->v.tbl || src16(k)) upl = 1;         // the table format and the 16-bit baselines run one unit per lane
     const bool std3 = upl == 1 && k == 3 && h->n_seg == 3 && lanerow_format(h->v, h->group_size, h->n_seg) &&
                       h->v.col_mask == 0xFFFFFFFFu;

@@ -61,6 +61,15 @@ inline bool lanerow_format(const MatView& v, int group_size, int n_seg) {
     return true;
 }
 
+// True when a table-format handle can run the lane-row kernels (standalone
+// SpMV): the exponent index in the column word and the 16/16/20 segments.
+inline bool lanerow_format_tbl(const MatView& v, int n_seg) {
+    if (!v.tbl || v.hi_mask != 0 || v.s1 != 16) return false;
+    if (n_seg >= 2 && v.s2 != 16) return false;
+    if (n_seg >= 3 && (v.s3 != 20 || v.r_lo != 4)) return false;
+    return true;
+}
+
 // Rows per lane at each value source: two at level 1 (the least decode work,
 // so more chains per warp pay), one elsewhere (wider decode: one row per lane
 // keeps more warps resident).
@@ -208,7 +217,10 @@ __device__ __forceinline__ double lr_ldx(const double* p, bool live) {
 
 // Nonzeros u0 .. u0 + N - 1 of the lane's R rows: every gather first (all in
 // flight), then the rows' FMA chains interleaved, each row in column order.
-template <int K, int N, int R, bool FAST>
+// TBL: the global exponent table with the index in the column word (Sec.
+// III-C; 0: the per-group format): columns are masked, and each value's
+// exponent is its table entry.
+template <int K, int N, int R, bool FAST, int TBL = 0>
 __device__ __forceinline__ void lr_batch(const MatView& m, const double* __restrict__ x, const unsigned char* st,
                                          const LrRows<R>& W, int u0, int wbase, double* acc) {
     using LY = LrLayout<K, R>;
@@ -217,7 +229,10 @@ __device__ __forceinline__ void lr_batch(const MatView& m, const double* __restr
 #pragma unroll
     for (int r = 0; r < R; r++) {
 #pragma unroll
-        for (int u = 0; u < N; u++) xv[r][u] = lr_ldx(x + scol[W.o[r] + u0 + u], u0 + u < W.len[r]);
+        for (int u = 0; u < N; u++) {
+            const int32_t c = scol[W.o[r] + u0 + u];
+            xv[r][u] = lr_ldx(x + (TBL ? col_of(m, c) : c), u0 + u < W.len[r]);
+        }
     }
     if constexpr (K == SRC_FP64) {
         const double* sv = reinterpret_cast<const double*>(st + LY::OFF_V);
@@ -266,14 +281,26 @@ __device__ __forceinline__ void lr_batch(const MatView& m, const double* __restr
                 if constexpr (FAST) {
                     // the nibble placed at bits 16..19 with one shift and a mask
                     const uint32_t nb16 = (4 * u <= 16 ? nib[r] << (16 - 4 * u) : nib[r] >> (4 * u - 16)) & 0xF0000u;
-                    a = lr_fast<K>(h, t1, t2, nb16, W.eoff[r]);
+                    uint32_t eoff = W.eoff[r];
+                    if constexpr (TBL != 0) {          // the value's own table entry
+                        const uint32_t ix = (uint32_t)((uint64_t)(uint32_t)scol[i] >> m.ei_shift);
+                        eoff = (uint32_t)((int)__ldg(m.etab + ix) - LR_EBIAS) << 20;
+                    }
+                    a = lr_fast<K>(h, t1, t2, nb16, eoff);
+                } else if constexpr (TBL != 0) {
+                    // the index bits of the column word (past a row's end a
+                    // stale word still gives an index below the table's 64)
+                    const uint32_t ix = (uint32_t)((uint64_t)(uint32_t)scol[i] >> m.ei_shift);
+                    a = lr_general<K>(m, h, t1, t2, nb, (int)__ldg(m.etab + ix));
                 } else {
                     const int Eg = u0 + u < W.len[r] ? (int)__ldg(m.gexp + ((W.rs[r] + u0 + u) >> 5)) : 0;
                     a = lr_general<K>(m, h, t1, t2, nb, Eg);
                 }
-                // past the row's end x reads 0 and the fast decoders give a
-                // finite value, so the FMA adds an exact zero (acc is never -0)
-                if (FAST || u0 + u < W.len[r]) acc[r] = fma(a, xv[r][u], acc[r]);
+                // past the row's end x reads 0 and the group format's fast
+                // decoders give a finite value, so the FMA adds an exact zero
+                // (acc is never -0); a table entry read through a stale column
+                // word may not, so the table format predicates the FMA
+                if ((FAST && TBL == 0) || u0 + u < W.len[r]) acc[r] = fma(a, xv[r][u], acc[r]);
             }
         }
     }
@@ -281,14 +308,14 @@ __device__ __forceinline__ void lr_batch(const MatView& m, const double* __restr
 
 // The lane's rows: batches of 8, then one batch of the warp's remaining length
 // (the longest row of the warp's tile).
-template <int K, int R, bool FAST>
+template <int K, int R, bool FAST, int TBL = 0>
 __device__ __forceinline__ void lr_rows(const MatView& m, const double* __restrict__ x, const unsigned char* st,
                                         const LrRows<R>& W, int maxlen, int wbase, double* acc) {
     int u0 = 0;
-    for (; u0 + 8 <= maxlen; u0 += 8) lr_batch<K, 8, R, FAST>(m, x, st, W, u0, wbase, acc);
+    for (; u0 + 8 <= maxlen; u0 += 8) lr_batch<K, 8, R, FAST, TBL>(m, x, st, W, u0, wbase, acc);
     switch (maxlen - u0) {
 #define GSE_LR_TAIL(NN) \
-    case NN: lr_batch<K, NN, R, FAST>(m, x, st, W, u0, wbase, acc); break;
+    case NN: lr_batch<K, NN, R, FAST, TBL>(m, x, st, W, u0, wbase, acc); break;
         GSE_LR_TAIL(7) GSE_LR_TAIL(6) GSE_LR_TAIL(5) GSE_LR_TAIL(4) GSE_LR_TAIL(3) GSE_LR_TAIL(2) GSE_LR_TAIL(1)
 #undef GSE_LR_TAIL
         default: break;
@@ -327,7 +354,7 @@ __device__ __forceinline__ bool lr_heads_nonzero(const unsigned char* st, int n8
 
 // The R rows of every lane of one staged tile whose slice starts at CSR
 // index e0 and ends at e1; rs[r], rt[r]: the lane's row r.
-template <int K, int R>
+template <int K, int R, int TBL = 0>
 __device__ __forceinline__ void lr_tile(const MatView& m, const double* __restrict__ x, const unsigned char* st, int e0, int e1, const int* rs, const int* rt,
                                         int lane, double* acc) {
     const unsigned FULL = 0xFFFFFFFFu;
@@ -345,7 +372,15 @@ __device__ __forceinline__ void lr_tile(const MatView& m, const double* __restri
     }
     const int maxlen = __reduce_max_sync(FULL, mx);
     const int wbase = (e0 >> 5) << 2;
-    if constexpr (K <= 3) {
+    if constexpr (K <= 3 && TBL == 1) {
+        lr_rows<K, R, false, 1>(m, x, st, W, maxlen, wbase, acc);
+    } else if constexpr (K <= 3 && TBL == 2) {
+        // every table entry exceeds W_1 (checked at launch): a value's leading
+        // one is in its head whenever the head magnitude is nonzero
+        const bool fast = K < 2 || lr_heads_nonzero<K, R>(st, ((e1 + 7) & ~7) - a8, lane);
+        if (fast) lr_rows<K, R, true, 2>(m, x, st, W, maxlen, wbase, acc);
+        else lr_rows<K, R, false, 2>(m, x, st, W, maxlen, wbase, acc);
+    } else if constexpr (K <= 3) {
         bool ok = true;
 #pragma unroll
         for (int r = 0; r < R; r++) ok = lr_row_fast(m, rs[r], rt[r], &W.eoff[r]) && ok;
@@ -354,7 +389,7 @@ __device__ __forceinline__ void lr_tile(const MatView& m, const double* __restri
         if (fast) lr_rows<K, R, true>(m, x, st, W, maxlen, wbase, acc);
         else lr_rows<K, R, false>(m, x, st, W, maxlen, wbase, acc);
     } else {
-        lr_rows<K, R, false>(m, x, st, W, maxlen, wbase, acc);
+        lr_rows<K, R, false, TBL>(m, x, st, W, maxlen, wbase, acc);
     }
 }
 
@@ -362,7 +397,7 @@ __device__ __forceinline__ void lr_tile(const MatView& m, const double* __restri
 // (ntile in all), through the warp's two stages at `wsm`.  Row and nonzero
 // indices are 32-bit (the CSR's row pointers are int32).  Returns the lane's
 // share of p.y (DOT) -- zero otherwise.
-template <int K, bool DOT, bool RESID, int R = lr_rows_per_lane<K>()>
+template <int K, bool DOT, bool RESID, int R = lr_rows_per_lane<K>(), int TBL = 0>
 __device__ __forceinline__ double lr_loop(const MatView& m, const double* __restrict__ x, const Epi& e, int64_t t0_,
                                           int64_t tstride_, int64_t ntile_, unsigned char* wsm) {
     constexpr int TILE = 32 * R;
@@ -405,7 +440,7 @@ __device__ __forceinline__ double lr_loop(const MatView& m, const double* __rest
         cpa_wait<1>();                      // tile t's copies (all but the newest group) have landed
         __syncwarp();
         double acc[R];
-        lr_tile<K, R>(m, x, wsm + s * SB, e0, cur.end, cur.a, rt, lane, acc);
+        lr_tile<K, R, TBL>(m, x, wsm + s * SB, e0, cur.end, cur.a, rt, lane, acc);
 #pragma unroll
         for (int r = 0; r < R; r++) {
             const int row = t * TILE + 32 * r + lane;

@@ -61,9 +61,10 @@ def test_table_encode_bit_exact(name, num_exp):
 
 @pytest.mark.parametrize("name", list(MATS))
 @pytest.mark.parametrize("sched", [1, gse.SCHEDULE_ROWS])
-def test_table_spmv_against_oracle(name, sched):
+@pytest.mark.parametrize("num_exp", [1, 8, 64])
+def test_table_spmv_against_oracle(name, sched, num_exp):
     A = MATS[name]()
-    M = gse.GseMatrix.from_csr(A, num_exp=8, attach=(64,))
+    M = gse.GseMatrix.from_csr(A, num_exp=num_exp, attach=(64,))
     try:
         M.set_schedule(sched)
     except gse.GseError as e:          # row blocks too wide for the row schedule
@@ -71,7 +72,7 @@ def test_table_spmv_against_oracle(name, sched):
         return
     x = synth.uniform_x(A.n_cols, seed=4)
     xd = torch.from_numpy(x).cuda()
-    table, levels = oracle.table_levels(A.val, 8, SEG)
+    table, levels = oracle.table_levels(A.val, num_exp, SEG)
     for k in (1, 2, 3):
         y = M.spmv(k, xd).cpu().numpy()
         check_spmv_rows(y, A, levels[k - 1], x)
