@@ -180,5 +180,9 @@ struct SpmvArgs {
 int launch_spmv(gse_matrix* h, int k, int epi, const SpmvArgs& a, cudaStream_t s, int upl_override = 0);
 // True when gse_spmv at level k runs the lane-row kernel on the row schedule.
 bool lanerow_ok(const gse_matrix* h, int k);
+// For a handle on the lane-row kernels: 0 the per-group format; 1 the exponent
+// table with its index in the column word (general decode); 2 the same with
+// every entry above W_1 (fast decode).
+int lanerow_table_kind(const gse_matrix* h);
 
 }  // namespace gse

@@ -218,10 +218,10 @@ __global__ void __launch_bounds__(ENG_ROW_WARPS * 32, 4) k_cg_p1_rows(const SysD
 
 // One lane-row pass as a separate (not inlined) function, so that the
 // p.Ap pass and the residual pass of a kernel get their registers each.
-template <int K, bool DOT, bool RESID>
+template <int K, bool DOT, bool RESID, int TBL = 0>
 __device__ __noinline__ double eng_lr_pass(const MatView& m, const double* x, const Epi& e, int64_t w0, int64_t ws,
                                            int64_t ntile, unsigned char* wsm) {
-    return lr_loop<K, DOT, RESID, 1>(m, x, e, w0, ws, ntile, wsm);
+    return lr_loop<K, DOT, RESID, 1, TBL>(m, x, e, w0, ws, ntile, wsm);
 }
 
 // Lane-row SpMV phase: warp w of a system's CTAs takes the 32-row tiles w,
@@ -229,23 +229,34 @@ __device__ __noinline__ double eng_lr_pass(const MatView& m, const double* x, co
 // its system runs.  Each level's pass is a separate function with its own
 // registers; the kernel itself holds little besides the system's matrix
 // view, which it stages in shared memory once per block.
-template <bool ITER>
+// TBL: the system's table kind (lr_tbl); the plain CSR baselines of a table
+// handle only mask their columns, so they take kind 1.
+template <bool ITER, int TBL = 0>
 __device__ __forceinline__ double eng_lanerow(int k, const MatView& m, const double* x, const Epi& e, int64_t w0,
                                               int64_t ws, int64_t ntile, unsigned char* smem) {
     const int warp = threadIdx.x >> 5;
+    constexpr int TB = TBL ? 1 : 0;
     switch (k) {
-#define GSE_LR_CASE(KK) \
-    case KK: return eng_lr_pass<KK, ITER, !ITER>(m, x, e, w0, ws, ntile, smem + warp * LR_STAGES * LrLayout<KK, 1>::BYTES);
-        GSE_LR_CASE(1)
-        GSE_LR_CASE(2)
-        GSE_LR_CASE(3)
-        GSE_LR_CASE(SRC_FP32)
-        GSE_LR_CASE(SRC_FP16)
-        GSE_LR_CASE(SRC_BF16)
-        GSE_LR_CASE(SRC_FP64)
+#define GSE_LR_CASE(KK, T) \
+    case KK: return eng_lr_pass<KK, ITER, !ITER, T>(m, x, e, w0, ws, ntile, smem + warp * LR_STAGES * LrLayout<KK, 1>::BYTES);
+        GSE_LR_CASE(1, TBL)
+        GSE_LR_CASE(2, TBL)
+        GSE_LR_CASE(3, TBL)
+        GSE_LR_CASE(SRC_FP32, TB)
+        GSE_LR_CASE(SRC_FP16, TB)
+        GSE_LR_CASE(SRC_BF16, TB)
+        GSE_LR_CASE(SRC_FP64, TB)
 #undef GSE_LR_CASE
         default: return 0.0;
     }
+}
+
+template <bool ITER>
+__device__ __forceinline__ double eng_lanerow_kind(int tbl, int k, const MatView& m, const double* x, const Epi& e,
+                                                   int64_t w0, int64_t ws, int64_t ntile, unsigned char* smem) {
+    if (tbl == 2) return eng_lanerow<ITER, 2>(k, m, x, e, w0, ws, ntile, smem);
+    if (tbl == 1) return eng_lanerow<ITER, 1>(k, m, x, e, w0, ws, ntile, smem);
+    return eng_lanerow<ITER, 0>(k, m, x, e, w0, ws, ntile, smem);
 }
 
 __global__ void __launch_bounds__(ENG_LR_WARPS * 32, 4) k_cg_p1_lr(const SysDesc* __restrict__ sys,
@@ -276,7 +287,7 @@ __global__ void __launch_bounds__(ENG_LR_WARPS * 32, 4) k_cg_p1_lr(const SysDesc
     const int64_t ntile = (S.n + 31) / 32;      // one row per lane in the engine
     const int64_t w0 = (int64_t)lb * ENG_LR_WARPS + (threadIdx.x >> 5), ws = (int64_t)nblk * ENG_LR_WARPS;
     if (mode == MODE_ITER) {
-        const double dot = eng_lanerow<true>(k, mv, x, e, w0, ws, ntile, smem);
+        const double dot = eng_lanerow_kind<true>(S.lr_tbl, k, mv, x, e, w0, ws, ntile, smem);
         double total;
         if (sys_grid_sum(dot, S.partial, S.counter, lb, nblk, red, &total) && threadIdx.x == 0) {
             const double alpha = st->rho / total;
@@ -285,7 +296,7 @@ __global__ void __launch_bounds__(ENG_LR_WARPS * 32, 4) k_cg_p1_lr(const SysDesc
             st->brk = !(total > 0.0) || !isfinite(total) || !isfinite(alpha);
         }
     } else {
-        eng_lanerow<false>(k, mv, x, e, w0, ws, ntile, smem);
+        eng_lanerow_kind<false>(S.lr_tbl, k, mv, x, e, w0, ws, ntile, smem);
     }
 }
 
@@ -330,7 +341,8 @@ __global__ void __launch_bounds__(ENG_LR_WARPS * 32, 4) k_cg_p1_lr_solo(const __
     Epi e;
     if (mode == MODE_ITER) {
         e.kind = EPI_CG_PQ; e.y = S.q; e.b = nullptr; e.p = S.p;
-        const double dot = solo_lr_iter(st->k, m, S.p, e, w0, ws, ntile, smem);
+        const double dot = S.lr_tbl ? eng_lanerow_kind<true>(S.lr_tbl, st->k, m, S.p, e, w0, ws, ntile, smem)
+                                    : solo_lr_iter(st->k, m, S.p, e, w0, ws, ntile, smem);
         double total;
         if (sys_grid_sum(dot, S.partial, S.counter, lb, nblk, red, &total) && threadIdx.x == 0) {
             const double alpha = st->rho / total;
@@ -349,7 +361,7 @@ __global__ void __launch_bounds__(ENG_LR_WARPS * 32, 4) k_cg_p1_lr_solo(const __
     } else {
         e.kind = EPI_RESID; e.y = S.q; e.b = S.b; e.p = nullptr; k = S.prm.kmax;
     }
-    eng_lanerow<false>(k, mv, S.x, e, w0, ws, ntile, smem);
+    eng_lanerow_kind<false>(S.lr_tbl, k, mv, S.x, e, w0, ws, ntile, smem);
 }
 
 // Dynamic shared memory of the lane-row P1 kernel for systems that run

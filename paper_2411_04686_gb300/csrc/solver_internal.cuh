@@ -33,6 +33,7 @@ struct SysDesc {
     int row_span;              // staged row kernel: 256-row span
     int lanerow;               // row schedule through the lane-row loop (spmv_lanerow.cuh)
     int lr_smem;               // lane-row: dynamic shared memory of its P1 CTAs
+    int lr_tbl;                // lane-row: 0 per-group format; 1 / 2 exponent table (general / fast decode)
     int vec2;                  // x, r, p, q 16-byte aligned: the vector phases load element pairs
     int64_t n, n_chunks;
     const double* b;
@@ -148,6 +149,7 @@ inline void sys_partition(SysDesc& d, const gse_matrix* h, int num_sms, int ksta
     d.sched = (h->schedule_forced ? h->schedule_forced : h->schedule_auto) == GSE_SCHEDULE_ROWS &&
                       h->row_span256 <= GSE_ROW_SPAN_MAX ? GSE_SCHEDULE_ROWS : 1;
     d.lanerow = d.sched == GSE_SCHEDULE_ROWS && lanerow_ok(h, kstart) && lanerow_ok(h, kmax) ? 1 : 0;
+    d.lr_tbl = d.lanerow ? lanerow_table_kind(h) : 0;
     d.row_span = h->row_span256;
     d.lr_smem = d.lanerow ? (int)p1_lr_smem(kstart, kmax) : 0;
     d.n = h->v.n_rows;

@@ -218,23 +218,17 @@ static bool lanerow_spans_ok(const gse_matrix* h) {
 }
 
 bool lanerow_ok(const gse_matrix* h, int k) {
-    // the table format keeps exponent indices in the column words: the CG
-    // engine's lane-row phase reads them as plain columns, so that format
-    // stays on the engine's other kernels (the standalone SpMV below takes it)
-    if (h->v.tbl || h->v.col_mask != 0xFFFFFFFFu) return false;
     if (!lanerow_spans_ok(h)) return false;
+    // the exponent table with its index in the column word: masked columns,
+    // per-value table exponents (an index in the head stays on other kernels)
+    if (h->v.tbl) return lanerow_format_tbl(h->v, h->n_seg);
+    if (h->v.col_mask != 0xFFFFFFFFu) return false;
     return k > 3 || lanerow_format(h->v, h->group_size, h->n_seg);
-}
-
-// The standalone SpMV's lane-row test: lanerow_ok, or the table format with
-// its index in the column word (masked columns, per-value table exponents).
-static bool lanerow_ok_spmv(const gse_matrix* h, int k) {
-    return lanerow_ok(h, k) || (lanerow_format_tbl(h->v, h->n_seg) && lanerow_spans_ok(h));
 }
 
 // 0: per-group format; 1: table, general decode; 2: table, every entry above
 // W_1 so a nonzero head holds the leading one (fast decode).
-static int lanerow_table_kind(const gse_matrix* h) {
+int lanerow_table_kind(const gse_matrix* h) {
     if (!h->v.tbl) return 0;
     for (int i = 0; i < h->num_exp; i++)
         if (h->etab_host[i] <= LR_W1) return 1;
@@ -370,7 +364,7 @@ static int resident_blocks(const KernelPick& kp) {
 int launch_spmv(gse_matrix* h, int k, int epi, const SpmvArgs& a, cudaStream_t s, int upl_override) {
     int upl = upl_override ? upl_override : units_per_lane(h);
     if (upl == GSE_SCHEDULE_ROWS)
-        return lanerow_ok_spmv(h, k) ? launch_lanerow(h, k, epi, a, s) : launch_rows(h, k, epi, a, s);
+        return lanerow_ok(h, k) ? launch_lanerow(h, k, epi, a, s) : launch_rows(h, k, epi, a, s);
     if (h->v.tbl || src16(k)) upl = 1;         // the table format and the 16-bit baselines run one unit per lane
     const bool std3 = upl == 1 && k == 3 && h->n_seg == 3 && lanerow_format(h->v, h->group_size, h->n_seg) &&
                       h->v.col_mask == 0xFFFFFFFFu;

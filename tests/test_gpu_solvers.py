@@ -93,9 +93,10 @@ def test_bounded_wait_timeout_is_reported_then_cleared():
     GSE_TIMEOUT by the solve, and the next solve on the same handle is clean.
     The handle's test flag makes its staged kernels issue no copy, so every
     wait runs out with nothing in flight (no fault, no hang).  The table
-    format on the row schedule runs the staged row kernel in the CG engine."""
+    format with its index in the head, on the row schedule, runs the staged row
+    kernel in the CG engine."""
     A = synth.poisson2d(32, 1.0 / 3.0)
-    M = gse.GseMatrix.from_csr(A, num_exp=8)
+    M = gse.GseMatrix.from_csr(A, num_exp=8, index_place=gse.INDEX_VALUE)
     M.set_schedule(gse.SCHEDULE_ROWS)
     b = _dev(synth.rhs_ones(A))
     short = gse.Policy(**{**gse.SCALED_CG.__dict__, "max_iter": 12})
@@ -106,7 +107,7 @@ def test_bounded_wait_timeout_is_reported_then_cleared():
     M.test_timeout(False)
     x = torch.zeros(A.n_rows, dtype=torch.float64, device="cuda")
     info = M.cg(b, x, tol=1e-10, policy=gse.SCALED_CG)
-    table, levels = oracle.table_levels(A.val, 8, (16, 16, 20))
+    table, levels = oracle.table_levels(A.val, 8, (16, 16, 20), index_in_value=True)
     ref = oracle.stepped_cg(A.row_ptr, A.col, levels, synth.rhs_ones(A), tol=1e-10, policy=oracle.SCALED_CG)
     assert info["status"] == gse.OK and info["rel_res_true"] < 1e-10
     for i in (1, 2):
